@@ -1,0 +1,194 @@
+"""CPU oracle (FP64 / exact integer) for brute-force de-dispersion and the
+boxcar threshold search -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The product library never loads it and shares
+no code with it.  The arithmetic lives in ``dd_oracle.c`` (plain loops, built
+with FMA contraction off); this module builds it with gcc and marshals numpy
+arrays through ctypes.
+
+Paper passages followed (Magro et al. 2011):
+  Eq. 1 (Section 1)        dispersion delay          -> delays()
+  Section 3, Eq. 2         maximum shift             -> delays(), maxshift_eq2()
+  Section 3.1              brute-force sum           -> dedisperse()
+  Section 3 (output thread) mean, sigma, n-sigma test -> stats(), search()
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dd_oracle.c")
+_LIB = os.path.join(_HERE, "libdd_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CAND_DTYPE = np.dtype([("dm_idx", np.int64), ("t", np.int64), ("width_idx", np.int64),
+                       ("snr", np.float64), ("value", np.float64)])
+
+
+def build(force: bool = False) -> str:
+    """Compile dd_oracle.c into libdd_oracle.so (gcc, -O2, no FMA contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+           "-shared", "-fopenmp", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = C.CDLL(_LIB)
+        i64, f64, vp = C.c_int64, C.c_double, C.c_void_p
+        lib.oracle_num_threads.restype = C.c_int
+        lib.oracle_set_threads.argtypes = [C.c_int]
+        lib.oracle_delay_exact.restype = f64
+        lib.oracle_delay_exact.argtypes = [f64, f64, i64, f64, f64, i64]
+        lib.oracle_delays.restype = C.c_int
+        lib.oracle_delays.argtypes = [i64, f64, f64, f64, vp, i64, vp, C.POINTER(i64)]
+        lib.oracle_maxshift_eq2.restype = f64
+        lib.oracle_maxshift_eq2.argtypes = [i64, f64, f64, f64, f64]
+        lib.oracle_half_to_double.restype = f64
+        lib.oracle_half_to_double.argtypes = [C.c_uint16]
+        for name in ("oracle_dedisperse_f32", "oracle_dedisperse_f16", "oracle_dedisperse_u8"):
+            getattr(lib, name).restype = None
+            getattr(lib, name).argtypes = [vp, i64, i64, vp, i64, i64, vp]
+        lib.oracle_point_f32.restype = f64
+        lib.oracle_point_f32.argtypes = [vp, i64, i64, vp, i64]
+        lib.oracle_row_f32.restype = None
+        lib.oracle_row_f32.argtypes = [vp, i64, i64, vp, i64, vp]
+        lib.oracle_stats_f64.argtypes = [vp, i64, C.POINTER(f64), C.POINTER(f64)]
+        lib.oracle_stats_i64.argtypes = [vp, i64, C.POINTER(f64), C.POINTER(f64)]
+        lib.oracle_threshold.restype = f64
+        lib.oracle_threshold.argtypes = [i64, f64, f64, f64]
+        for name in ("oracle_search_f64", "oracle_search_i64"):
+            getattr(lib, name).restype = i64
+            getattr(lib, name).argtypes = [vp, i64, i64, vp, i64, f64, f64, f64, vp, i64]
+        _lib = lib
+        return lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def set_threads(n: int) -> None:
+    _load().oracle_set_threads(int(n))
+
+
+def delay_exact(fch1, foff, nchans, tsamp, dm, c) -> float:
+    """Fractional delay in samples of channel c at DM dm (Eq. 1 / tsamp)."""
+    return float(_load().oracle_delay_exact(fch1, foff, nchans, tsamp, dm, c))
+
+
+def delays(nchans: int, fch1: float, foff: float, tsamp: float, dm_list) -> tuple:
+    """Integer delay table [ndm][nchans] (int64) and maxshift (Eq. 1, rounded)."""
+    dm = np.ascontiguousarray(np.asarray(dm_list, dtype=np.float64))
+    d = np.empty((dm.size, nchans), dtype=np.int64)
+    m = C.c_int64(0)
+    rc = _load().oracle_delays(nchans, fch1, foff, tsamp, _p(dm), dm.size, _p(d), C.byref(m))
+    if rc != 0:
+        raise ValueError("oracle_delays: invalid arguments")
+    return d, int(m.value)
+
+
+def maxshift_eq2(nchans, fch1, foff, tsamp, dm_max) -> float:
+    """Eq. 2 derivative approximation of the maximum shift (sanity bound only)."""
+    return float(_load().oracle_maxshift_eq2(nchans, fch1, foff, tsamp, dm_max))
+
+
+def half_to_double(bits: int) -> float:
+    return float(_load().oracle_half_to_double(int(bits)))
+
+
+def dedisperse(data: np.ndarray, delay_table: np.ndarray, nout: int) -> np.ndarray:
+    """Brute-force sum (Section 3.1).
+
+    data: [nchans][pitch] float32, uint16 (binary16 bit patterns) or uint8.
+    Returns [ndm][nout] float64 for float input, int64 for uint8.
+    """
+    lib = _load()
+    data = np.ascontiguousarray(data)
+    dl = np.ascontiguousarray(delay_table, dtype=np.int64)
+    nchans, pitch = data.shape
+    ndm = dl.shape[0]
+    assert dl.shape[1] == nchans
+    if nout < 0 or (nout > 0 and int(dl.max()) + nout > pitch):
+        raise ValueError("input too short for nout + maxshift")
+    if data.dtype == np.float32:
+        out = np.empty((ndm, nout), np.float64)
+        lib.oracle_dedisperse_f32(_p(data), pitch, nchans, _p(dl), ndm, nout, _p(out))
+    elif data.dtype == np.uint16:
+        out = np.empty((ndm, nout), np.float64)
+        lib.oracle_dedisperse_f16(_p(data), pitch, nchans, _p(dl), ndm, nout, _p(out))
+    elif data.dtype == np.uint8:
+        out = np.empty((ndm, nout), np.int64)
+        lib.oracle_dedisperse_u8(_p(data), pitch, nchans, _p(dl), ndm, nout, _p(out))
+    else:
+        raise TypeError(f"unsupported input dtype {data.dtype}")
+    return out
+
+
+def point_f32(data: np.ndarray, delay_row: np.ndarray, t: int) -> float:
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    row = np.ascontiguousarray(delay_row, dtype=np.int64)
+    return float(_load().oracle_point_f32(_p(data), data.shape[1], data.shape[0], _p(row), int(t)))
+
+
+def row_f32(data: np.ndarray, delay_row: np.ndarray, nout: int) -> np.ndarray:
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    row = np.ascontiguousarray(delay_row, dtype=np.int64)
+    out = np.empty(nout, np.float64)
+    _load().oracle_row_f32(_p(data), data.shape[1], data.shape[0], _p(row), int(nout), _p(out))
+    return out
+
+
+def stats(out: np.ndarray) -> tuple:
+    """(mu, sigma): population mean and std over the whole buffer, two-pass double."""
+    lib = _load()
+    x = np.ascontiguousarray(out)
+    mu, sg = C.c_double(0), C.c_double(0)
+    if x.dtype == np.int64:
+        lib.oracle_stats_i64(_p(x), x.size, C.byref(mu), C.byref(sg))
+    else:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        lib.oracle_stats_f64(_p(x), x.size, C.byref(mu), C.byref(sg))
+    return float(mu.value), float(sg.value)
+
+
+def threshold(w: int, mu: float, sigma: float, k: float) -> float:
+    return float(_load().oracle_threshold(int(w), mu, sigma, k))
+
+
+def search(out: np.ndarray, widths, mu: float, sigma: float, k: float,
+           cap: int = 1 << 20) -> np.ndarray:
+    """Boxcar threshold search; returns a structured array sorted by (dm, t, width_idx)."""
+    lib = _load()
+    x = np.ascontiguousarray(out)
+    ndm, nout = x.shape
+    w = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+    cands = np.empty(cap, dtype=CAND_DTYPE)
+    if x.dtype == np.int64:
+        n = lib.oracle_search_i64(_p(x), ndm, nout, _p(w), w.size, mu, sigma, k, _p(cands), cap)
+    else:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        n = lib.oracle_search_f64(_p(x), ndm, nout, _p(w), w.size, mu, sigma, k, _p(cands), cap)
+    if n > cap:
+        raise OverflowError(f"oracle search found {n} candidates > cap {cap}")
+    return cands[:n].copy()

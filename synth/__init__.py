@@ -1,0 +1,152 @@
+"""Seeded synthetic filterbank inputs shared by the tests, the benchmark and smoke().
+
+This module holds no de-dispersion arithmetic.  It draws noise, quantises it, and
+adds square pulses at per-channel sample offsets that the CALLER supplies (the
+tests take those offsets from the CPU oracle's delay table, the benchmark from
+the library's plan).  The workloads mirror the paper's test data: Gaussian noise
+of mean 0 and standard deviation 1 per channel plus square pulses whose height
+per channel sets the frequency-integrated S/N (Section 4, the fake-pulsar test
+of Table 2).
+
+Every generator is deterministic in its seed (numpy PCG64).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, List, Optional, Sequence
+
+import numpy as np
+
+__all__ = [
+    "Workload", "Pulse", "WORKLOADS", "workload", "noise_f32", "quantize_u8",
+    "to_f16_bits", "inject_pulses", "draw_pulses", "pulse_amplitude",
+    "aligned_pitch",
+]
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    """Plan parameters of one synthetic search, in the paper's units.
+
+    fch1/foff in MHz (foff < 0: descending band, channel 0 is the top), tsamp in
+    seconds, DM in pc cm^-3.  dm_list is built as i*dm_step in double, exactly
+    as the pulse injection reads it back.
+    """
+    name: str
+    nchans: int
+    fch1: float
+    foff: float
+    tsamp: float
+    nsamp: int
+    ndm: int
+    dm_step: float
+    widths: tuple
+    sigma: float = 6.0
+    seed: int = 0
+    dm_start: float = 0.0
+
+    @property
+    def dm_list(self) -> np.ndarray:
+        i = np.arange(self.ndm, dtype=np.float64)
+        return self.dm_start + i * self.dm_step
+
+
+# Small FP32 case (fits the oracle in seconds), the LOFAR-like single beam,
+# and the uint8 / FP16 precision cases share the first shape.
+WORKLOADS = {
+    "small_f32": Workload("small_f32", nchans=128, fch1=150.0, foff=-0.1953125,
+                          tsamp=327.68e-6, nsamp=8192, ndm=64, dm_step=0.1,
+                          widths=(1, 2, 4, 8), seed=1),
+    "lofar_f32": Workload("lofar_f32", nchans=1024, fch1=150.0, foff=-0.01171875,
+                          tsamp=163.84e-6, nsamp=1 << 20, ndm=2000, dm_step=0.05,
+                          widths=(1, 2, 4, 8, 16, 32), seed=2),
+}
+
+
+def workload(name: str) -> Workload:
+    return WORKLOADS[name]
+
+
+def aligned_pitch(nsamp: int, elem_bytes: int, align: int = 16) -> int:
+    """Smallest row pitch (in elements) >= nsamp whose byte size is a multiple of align."""
+    per = max(1, align // elem_bytes)
+    return ((nsamp + per - 1) // per) * per
+
+
+def noise_f32(nchans: int, nsamp: int, seed: int, pitch: Optional[int] = None) -> np.ndarray:
+    """Channel-major float32 N(0,1) noise, shape [nchans][pitch]; padding columns are 0."""
+    pitch = nsamp if pitch is None else pitch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = np.zeros((nchans, pitch), dtype=np.float32)
+    for c in range(nchans):
+        out[c, :nsamp] = rng.standard_normal(nsamp, dtype=np.float32)
+    return out
+
+
+def quantize_u8(x: np.ndarray, mean: float = 128.0, std: float = 16.0) -> np.ndarray:
+    """q = clip(rint(mean + std*x), 0, 255) as uint8 (the 8-bit digitiser model)."""
+    return np.clip(np.rint(mean + std * x.astype(np.float64)), 0, 255).astype(np.uint8)
+
+
+def to_f16_bits(x: np.ndarray) -> np.ndarray:
+    """Round float32 data to IEEE binary16 and return the raw 16-bit patterns."""
+    return x.astype(np.float16).view(np.uint16)
+
+
+@dataclasses.dataclass
+class Pulse:
+    dm: float        # the DM value the offsets were computed for
+    t0: int          # arrival sample in the top (reference) channel
+    width: int       # samples
+    amp: float       # height per channel per sample
+
+
+def pulse_amplitude(snr: float, nchans: int, width: int) -> float:
+    """Per-channel height giving boxcar S/N `snr` for unit-variance noise.
+
+    A square pulse of height a and width w summed over C channels gives a
+    signal a*C*w against noise sqrt(C*w): S/N = a*sqrt(C*w).  (The paper's
+    fake-pulsar file uses height 8/sqrt(1024) = 0.25 for a per-sample S/N of 8.)
+    """
+    return snr / math.sqrt(nchans * width)
+
+
+def inject_pulses(data: np.ndarray, pulses: Sequence[Pulse],
+                  offsets_for: Callable[[float], np.ndarray], nsamp: int) -> None:
+    """Add square pulses in place.
+
+    offsets_for(dm) must return the per-channel integer arrival offsets (int64,
+    length nchans) of a pulse at that DM; the pulse covers samples
+    t0 + offsets[c] + j for j < width in channel c.  Samples past nsamp are
+    dropped.
+    """
+    nchans = data.shape[0]
+    for p in pulses:
+        off = np.asarray(offsets_for(p.dm), dtype=np.int64)
+        assert off.shape == (nchans,)
+        for c in range(nchans):
+            s = p.t0 + int(off[c])
+            e = min(s + p.width, nsamp)
+            if s < nsamp and e > s:
+                data[c, s:e] += np.asarray(p.amp, dtype=data.dtype)
+
+
+def draw_pulses(n: int, dm_lo: float, dm_hi: float, width_lo: int, width_hi: int,
+                snr_lo: float, snr_hi: float, t_hi: int, nchans: int,
+                seed: int, min_sep: int = 64) -> List[Pulse]:
+    """Draw n non-overlapping pulses: DM ~ U(dm_lo, dm_hi) (off-grid allowed),
+    width ~ U{width_lo..width_hi}, S/N ~ U(snr_lo, snr_hi), t0 ~ U[0, t_hi]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out: List[Pulse] = []
+    taken: List[int] = []
+    while len(out) < n:
+        dm = float(rng.uniform(dm_lo, dm_hi))
+        w = int(rng.integers(width_lo, width_hi + 1))
+        snr = float(rng.uniform(snr_lo, snr_hi))
+        t0 = int(rng.integers(0, t_hi + 1))
+        if any(abs(t0 - u) < min_sep + w for u in taken):
+            continue
+        taken.append(t0)
+        out.append(Pulse(dm=dm, t0=t0, width=w, amp=pulse_amplitude(snr, nchans, w)))
+    return out
