@@ -1,0 +1,317 @@
+#!/usr/bin/env python3
+"""Benchmark: brute-force de-dispersion + boxcar search on the LOFAR-like
+single beam (1024 channels, 150 MHz top, 12 MHz band, 163.84 us, 2^20
+samples, 2000 DM trials 0..99.95 step 0.05, 16 injected pulses), one GB300.
+
+One step = dd_execute (Section 3.1 sum, fused partial statistics) + dd_search
+(statistics finalisation, boxcar sums, threshold, compaction, candidate
+readback) on device-resident input.  Prints ONE JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (FP64, plain loops, all host cores) on a
+bounded sample of the same workload.  Under torchrun every rank processes its
+own beam of the same shape (weak scaling, no data-path collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "DM-trial·samples/s"
+WORKLOAD = "lofar_f32"
+
+
+def _pulses(wl, nout, seed):
+    return synth.draw_pulses(16, 0.0, wl.dm_list[-1], 1, 32, 8.0, 20.0, nout - 32, wl.nchans, seed)
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region (SM clock, throttle reasons)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_reference(args, rank, world):
+    """CPU oracle on a bounded sample of the same workload (rank 0 only)."""
+    import oracle
+    if rank != 0:
+        return
+    wl = synth.workload(WORKLOAD)
+    oracle.build()
+    d_all, m = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
+    ndm_s, nt_s = 32, 16384         # 32 DM rows spread over the range x 16384 samples
+    rows = np.linspace(0, wl.ndm - 1, ndm_s).astype(np.int64)
+    d = np.ascontiguousarray(d_all[rows])
+    x = synth.noise_f32(wl.nchans, nt_s + m, seed=wl.seed)
+    cores = oracle.num_threads()
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        out = oracle.dedisperse(x, d, nt_s)
+        mu, sg = oracle.stats(out)
+        oracle.search(out, list(wl.widths), mu, sg, wl.sigma)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    tm = statistics.median(times)
+    value = ndm_s * nt_s / tm
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tm * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "lofar_f32: 1024 ch, 150 MHz top, foff -0.01171875 MHz, "
+                   "tsamp 163.84 us, 2^20 samples, 2000 DMs 0-99.95 step 0.05",
+                   "sample": f"{ndm_s} DM rows x {nt_s} samples per step"},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
+                         "sample": f"{ndm_s} of 2000 DM rows x {nt_s} of 1028179 samples, "
+                                   "dedisperse + stats + search"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline_sample():
+    """Oracle on a bounded sample (about 10-30 s of CPU work), for the GPU line."""
+    import oracle
+    wl = synth.workload(WORKLOAD)
+    oracle.build()
+    d_all, m = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
+    ndm_s, nt_s = 32, 16384
+    rows = np.linspace(0, wl.ndm - 1, ndm_s).astype(np.int64)
+    d = np.ascontiguousarray(d_all[rows])
+    x = synth.noise_f32(wl.nchans, nt_s + m, seed=wl.seed)
+    t0 = time.perf_counter()
+    out = oracle.dedisperse(x, d, nt_s)
+    mu, sg = oracle.stats(out)
+    oracle.search(out, list(wl.widths), mu, sg, wl.sigma)
+    dt = time.perf_counter() - t0
+    return {"value": ndm_s * nt_s / dt, "unit": METRIC, "cores": oracle.num_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"{ndm_s} of 2000 DM rows x {nt_s} samples: dedisperse + stats + search"}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    import paper_1107_2516_gb300 as dd
+    from paper_1107_2516_gb300 import build as ddbuild
+
+    torch.cuda.set_device(local_rank)
+    if rank == 0 or world == 1:
+        ddbuild.build()
+    if world > 1:
+        dist.barrier()
+    dd.load()
+    wl = synth.workload(WORKLOAD)
+    plan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, wl.sigma,
+                   dd.DD_F32, wl.nsamp)
+    if args.kernel:
+        plan.set_kernel(args.kernel)
+    nout, M = plan.nsamp_out, plan.maxshift
+    # input: seeded noise + 16 pulses placed with the plan's own delay law
+    x = synth.noise_f32(wl.nchans, wl.nsamp, seed=wl.seed + 1000 * rank)
+    pulses = _pulses(wl, nout, seed=wl.seed + 1000 * rank)
+    pplan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, [p.dm for p in pulses], [1], 6.0,
+                    dd.DD_F32, wl.nsamp)
+    ptab = pplan.delays().astype(np.int64)
+    pplan.close()
+    lookup = {p.dm: ptab[i] for i, p in enumerate(pulses)}
+    synth.inject_pulses(x, pulses, lambda dm: lookup[dm], wl.nsamp)
+    host = torch.from_numpy(x)
+    xin = host.cuda()
+    out = torch.empty(wl.ndm * nout, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        plan.execute(xin, wl.nsamp, out, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        return plan.search(out, capacity=1 << 16, stream=stream)
+
+    for _ in range(args.warmup):
+        cands, total = step()
+    torch.cuda.synchronize()
+    ev_steps = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(torch.cuda.current_device())
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    g0.record(stream)
+    for i in range(args.steps):
+        cands, total = step(ev_steps[i])
+    g1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    total_ms = g0.elapsed_time(g1)
+    ker_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_steps)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    units_per_rank = wl.ndm * nout
+    value = units_per_rank * world / (ms_per_step / 1e3)
+
+    # end to end through the C ABI with host input (H2D + execute + search + readback)
+    pinned = host.pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        plan.process_host(pinned, wl.nsamp, capacity=1 << 16, stream=stream)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    n_e2e = max(2, args.steps // 2)
+    for _ in range(n_e2e):
+        c2, n2 = plan.process_host(pinned, wl.nsamp, capacity=1 << 16, stream=stream)
+    e2e_s = (time.perf_counter() - e0) / n_e2e
+    e2e_value = units_per_rank * world / e2e_s
+
+    kernel_id = plan.kernel
+    plan.close()
+    del out, xin
+    if rank != 0:
+        return
+    peaks = _peaks()
+    sm = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    adds = float(wl.ndm) * nout * wl.nchans
+    achieved = adds / (ker_ms / 1e3) / 1e9             # G channel-adds / s
+    peak = sm * 128 * sm_max * 1e6 / 1e9               # FP32 lanes x max clock
+    roof = {"bound": "alu", "kernel": f"dd kernel {kernel_id} (de-dispersion)",
+            "achieved": achieved, "peak": peak, "unit": "Gadd/s", "frac": achieved / peak,
+            "peak_basis": f"{sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",
+            "traffic": None,
+            "kernel_ms": ker_ms}
+    if clk.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (sm * 128 * clk["sm_mhz"] * 1e6 / 1e9)
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "lofar_f32: 1024 ch, fch1 150 MHz, foff -0.01171875 MHz, "
+                   "tsamp 163.84 us, nsamp 2^20, 2000 DMs 0-99.95 step 0.05, widths 1..32, 6 sigma",
+                   "nsamp_out": nout, "maxshift": M, "l2": "inputs larger than L2 (4.3 GB in, 8.2 GB out)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "real_time_factor": (nout * wl.tsamp) / (ms_per_step / 1e3),
+        "dedisp_ms": ker_ms, "search_ms": ms_per_step - ker_ms,
+        "candidates": int(total),
+        "e2e": {"value": e2e_value, "unit": METRIC,
+                "h2d_bytes_per_step": int(wl.nchans * wl.nsamp * 4),
+                "d2h_bytes_per_step": int(8 + 32 * min(total, 1 << 16) + 272)},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk,
+        "roofline": roof,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample()
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+/*
+ * dd.h -- C ABI of libdd: brute-force incoherent de-dispersion and a boxcar
+ * single-pulse threshold search on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Magro et al. 2011, "Real-time, fast radio transient searches with
+ * GPU de-dispersion".
+ *   Eq. 1 (Section 1)   delay between frequencies f1, f2 (MHz):
+ *                       4.15e6 ms * (f1^-2 - f2^-2) * DM
+ *   Section 3, Eq. 2    n outputs need n + maxshift input samples
+ *   Section 3.1         brute force: each output sample is the sum over all
+ *                       channels of the input shifted by its delay
+ *   Section 3           mean/std over the processed buffer, n-sigma threshold,
+ *                       (time, DM, intensity) candidates
+ *
+ * Definitions used by every call (C = nchans, D = ndm):
+ *   f_c      = fch1 + c*foff                     channel centre, MHz
+ *   f_top    = max_c f_c
+ *   d(c,dm)  = round(((4.15e6*DM) * (1/f_c^2 - 1/f_top^2)) / (tsamp*1e3))
+ *              evaluated in IEEE double, FMA contraction off, rounded half
+ *              away from zero                     (Eq. 1 over the sample time)
+ *   maxshift = max_{c,dm} d(c,dm)                (the exact form of Eq. 2)
+ *   nsamp_out = nsamp_in - maxshift
+ *   out[dm][t] = sum_{c=0}^{C-1} in[c][t + d(c,dm)],  0 <= t < nsamp_out
+ *   mu, sigma  = population mean / std over all D*nsamp_out values of out
+ *   B_w(dm,t)  = sum_{j<w} out[dm][t+j]  for t + w <= nsamp_out
+ *   candidate iff B_w > w*mu + sigma_k*sigma*sqrt(w)   (strict)
+ *   snr        = (B_w - w*mu) / (sigma*sqrt(w))
+ *
+ * Layouts.  `in` is channel-major: in[c*in_pitch + t], t contiguous, element
+ * type float32, uint8 or IEEE binary16 (DD_F32 / DD_U8 / DD_F16).  `out` is
+ * row-major [D][nsamp_out] with no padding: float32 for DD_F32 and DD_F16
+ * input (FP32 accumulation), int32 for DD_U8 input (exact integer sums).
+ *
+ * Ownership.  The caller owns `in`, `out` (device memory) and the host
+ * candidate array.  A plan owns its delay table, its statistics and candidate
+ * scratch on the device and its pinned host staging; dd_plan_destroy frees
+ * them.  A plan lives on the device that was current when it was created.
+ *
+ * Errors.  Every call returns a dd_status; none aborts.  On failure
+ * dd_last_error() returns a message for the calling thread.  Calls on one
+ * plan must not run concurrently from several host threads.
+ *
+ * Units: MHz, seconds, pc cm^-3 (the paper's units, Eq. 1).
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DD_API __attribute__((visibility("default")))
+#else
+#define DD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_plan dd_plan;
+
+typedef enum { DD_F32 = 0, DD_U8 = 1, DD_F16 = 2 } dd_dtype;
+
+typedef enum {
+    DD_OK = 0,
+    DD_ERR_ARG = 1,       /* invalid argument; nothing was launched          */
+    DD_ERR_NOMEM = 2,     /* a device or pinned allocation failed            */
+    DD_ERR_CUDA = 3,      /* a CUDA runtime call failed                      */
+    DD_ERR_OVERFLOW = 4,  /* more candidates than the caller's capacity      */
+    DD_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up              */
+    DD_ERR_BUDGET = 6     /* admission refused: the HBM budget is exhausted  */
+} dd_status;
+
+/* One search hit (32 bytes).  value is B_w exactly as summed on the device
+ * (an integer for DD_U8 plans); snr as defined above, in double, rounded to
+ * float. */
+typedef struct {
+    int32_t dm_idx;       /* index into the plan's dm_list                   */
+    int32_t width_idx;    /* index into the plan's boxcar_widths             */
+    int64_t t;            /* first sample of the boxcar, 0-based in out      */
+    float snr;
+    float reserved;
+    double value;
+} dd_candidate;
+
+/* Create a plan (Eq. 1 delays, Eq. 2 maxshift, Section 3.1 sum, Section 3
+ * search).  dm_list[ndm] (>= 0, any order) and boxcar_widths[nwidths]
+ * (1 <= w <= nsamp_out) are copied.  sigma_k is the threshold multiple.
+ * Requires nchans >= 1, ndm >= 1, tsamp_s > 0, fch1 > 0, the lowest channel
+ * centre > 0, nsamp_in > maxshift.  The delay table is computed here once,
+ * in double on the host, and uploaded as int32.  Returns DD_ERR_ARG for
+ * invalid arguments, DD_ERR_NOMEM / DD_ERR_CUDA on allocation failure. */
+DD_API int dd_plan_create(int32_t nchans, double fch1_mhz, double foff_mhz, double tsamp_s,
+                   const double *dm_list, int32_t ndm,
+                   const int32_t *boxcar_widths, int32_t nwidths, double sigma_k,
+                   int32_t in_dtype, int64_t nsamp_in, dd_plan **plan_out);
+
+/* Free everything the plan owns (synchronises the plan's device first).
+ * NULL is accepted. */
+DD_API int dd_plan_destroy(dd_plan *plan);
+
+/* Report maxshift and nsamp_out; when delays_host is not NULL, copy the
+ * int32 delay table d[dm][c] (ndm*nchans entries) into it.  Any output
+ * pointer may be NULL. */
+DD_API int dd_plan_info(const dd_plan *plan, int64_t *maxshift, int64_t *nsamp_out,
+                 int32_t *delays_host);
+
+/* Section 3.1: out[dm][t] = sum_c in[c][t + d(c,dm)] for all dm and
+ * 0 <= t < nsamp_out, plus per-block partial statistics kept in the plan for
+ * the next dd_search.  in_dev: device pointer, channel-major, in_pitch
+ * elements per channel row (in_pitch >= nsamp_in).  out_dev: device pointer
+ * to D*nsamp_out float32 (int32 for DD_U8).  stream: a cudaStream_t (NULL =
+ * legacy default stream).  Asynchronous: returns after the launches are
+ * queued.  The input buffers must not alias. */
+DD_API int dd_execute(dd_plan *plan, const void *in_dev, int64_t in_pitch, void *out_dev,
+               void *stream);
+
+/* Section 3 output stage, generalised to boxcars: statistics over the whole
+ * buffer, thresholds, boxcar sums, compaction.  out_dev is the buffer the
+ * last dd_execute on this plan wrote (if it is another buffer the statistics
+ * are recomputed from it).  Synchronises `stream`.  Writes up to `capacity`
+ * candidates to cand_host sorted by (dm_idx, t, width_idx) and the true count
+ * to *n_found.  If the true count exceeds capacity, the array holds an
+ * unspecified subset of `capacity` hits (sorted) and DD_ERR_OVERFLOW is
+ * returned. */
+DD_API int dd_search(dd_plan *plan, const void *out_dev, dd_candidate *cand_host,
+              int64_t capacity, int64_t *n_found, void *stream);
+
+/* mu and sigma used by the last dd_search on this plan (Section 3). */
+DD_API int dd_last_stats(const dd_plan *plan, double *mu, double *sigma);
+
+/* End-to-end call with HOST buffers: copies in_host (pinned or pageable,
+ * channel-major, in_pitch elements per row) to the device, runs dd_execute
+ * and dd_search, and returns the candidates as dd_search does.  The plan
+ * allocates its device staging for `in` and `out` on the first call and
+ * keeps it until dd_plan_destroy.  Synchronises `stream`. */
+DD_API int dd_process_host(dd_plan *plan, const void *in_host, int64_t in_pitch,
+                    dd_candidate *cand_host, int64_t capacity, int64_t *n_found,
+                    void *stream);
+
+/* Select the de-dispersion kernel for a plan: 0 = automatic (default),
+ * 1 = generic shared-memory kernel, 2 = register-blocked kernel.  Returns
+ * DD_ERR_ARG if the requested kernel cannot run this plan. */
+DD_API int dd_plan_set_kernel(dd_plan *plan, int32_t kernel);
+
+/* Kernel that dd_execute will launch for this plan (1 or 2, see above). */
+DD_API int dd_plan_get_kernel(const dd_plan *plan, int32_t *kernel);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+DD_API const char *dd_last_error(void);
+
+/* Library version string. */
+DD_API const char *dd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

@@ -1,0 +1,13 @@
+"""GB300-native brute-force incoherent de-dispersion and boxcar single-pulse
+search (Magro et al. 2011, Section 3.1 and Section 3), behind the C ABI of
+libdd.so (include/dd.h).  This package is the thin Python binding; the
+library is built in-tree by ``paper_1107_2516_gb300.build.build()``.
+"""
+from .dd import (CANDIDATE_DTYPE, DD_F16, DD_F32, DD_U8, DDError, EXPORTS, Plan, dd_execute,
+                 dd_last_error, dd_last_stats, dd_plan_create, dd_plan_destroy, dd_plan_get_kernel,
+                 dd_plan_info, dd_plan_set_kernel, dd_process_host, dd_search, dd_version, load)
+
+__all__ = ["CANDIDATE_DTYPE", "DD_F16", "DD_F32", "DD_U8", "DDError", "EXPORTS", "Plan",
+           "dd_execute", "dd_last_error", "dd_last_stats", "dd_plan_create", "dd_plan_destroy",
+           "dd_plan_get_kernel", "dd_plan_info", "dd_plan_set_kernel", "dd_process_host",
+           "dd_search", "dd_version", "load"]

@@ -1,0 +1,107 @@
+// Internal declarations shared by the libdd translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "dd.h"
+
+namespace dd {
+
+// Per-block partial statistics written by the de-dispersion kernels.
+// Floating point: (count, mean, M2) merged with the pairwise update of
+// Chan, Golub & LeVeque.  Integer: exact (count, sum, sum of squares).
+struct StatF { double n, mean, m2; };
+struct StatI { long long n, sum; unsigned long long sumsq; };
+
+// Device-side result of the statistics finalisation.
+struct SearchParams {
+    double mu, sigma;
+    int nw;                      // number of boxcar widths
+    int pad_;
+    float thr_f[64];             // largest float <= T_w (FP compare is then exact)
+    long long thr_i[64];         // floor(T_w) (integer compare is then exact)
+};
+
+constexpr int kMaxWidths = 64;
+
+// Tile shape of the generic kernel (kernel 1).
+constexpr int kGenDms = 16;      // DM trials per block
+constexpr int kGenThreads = 256; // threads per block
+constexpr int kGenTimes = 2;     // samples per thread (strided by kGenThreads)
+constexpr int kGenTile = kGenThreads * kGenTimes;
+
+// Register-blocked kernel (kernel 2) constants live in dd_fast.cu.
+
+}  // namespace dd
+
+struct dd_plan {
+    // problem
+    int32_t nchans = 0, ndm = 0, nwidths = 0;
+    dd_dtype dtype = DD_F32;
+    double fch1 = 0, foff = 0, tsamp = 0, sigma_k = 0;
+    int64_t nsamp_in = 0, maxshift = 0, nsamp_out = 0;
+    std::vector<double> dm_list;
+    std::vector<int32_t> widths;
+    std::vector<int32_t> delays;           // host copy [ndm][nchans]
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+
+    // kernel selection
+    int32_t kernel_req = 0;                // 0 auto
+    int32_t kernel = 1;                    // resolved
+
+    // device data
+    int32_t *d_gen = nullptr;              // kernel-1 tables: offsets | base | span
+    // generic kernel geometry
+    int gen_stride = 0;                    // smem row stride (floats)
+    int gen_chunk = 0;                     // channels per smem stage (0: no smem)
+    size_t gen_smem = 0;
+    // statistics partials of the last dd_execute
+    void *d_partials = nullptr;            // StatF or StatI per block
+    int64_t n_partials_cap = 0;
+    int64_t n_partials = 0;
+    const void *stats_out = nullptr;       // out buffer the partials describe
+    // search
+    dd::SearchParams *d_params = nullptr;
+    int32_t *d_wsorted = nullptr;          // widths sorted ascending: [nw] widths, [nw] indices
+    dd_candidate *d_cands = nullptr;
+    int64_t cand_cap = 0;
+    unsigned long long *d_count = nullptr;
+    unsigned long long *h_count = nullptr; // pinned
+    dd::SearchParams *h_params = nullptr;  // pinned
+    double last_mu = 0, last_sigma = 0;
+    // end-to-end staging (dd_process_host)
+    void *d_in_stage = nullptr;
+    size_t in_stage_bytes = 0;
+    void *d_out_stage = nullptr;
+    size_t out_stage_bytes = 0;
+
+    // register-blocked kernel data (kernel 2)
+    void *fast = nullptr;
+};
+
+namespace dd {
+
+int set_error(int code, const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+size_t in_elem_bytes(dd_dtype t);
+
+// dd_kernels.cu
+int generic_configure(dd_plan *p);
+int generic_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStream_t s);
+int stats_from_out(dd_plan *p, const void *out, cudaStream_t s);
+int search_launch(dd_plan *p, const void *out, cudaStream_t s);
+
+// dd_fast.cu
+int fast_configure(dd_plan *p);
+int fast_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStream_t s);
+void fast_release(dd_plan *p);
+
+}  // namespace dd

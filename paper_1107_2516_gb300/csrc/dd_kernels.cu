@@ -1,0 +1,606 @@
+// Generic de-dispersion kernel (kernel 1), statistics and the boxcar
+// threshold search.
+//
+// Section 3.1 (brute force): out[dm][t] = sum_c in[c][t + d(c,dm)].
+// Section 3 (output stage): mean and standard deviation over the whole
+// processed buffer, an n-sigma threshold, every point above it reported.
+#include "dd_internal.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace dd {
+
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<uint8_t>(uint8_t v) { return (float)v; }
+template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+
+// ---------------------------------------------------------------------------
+// Block-level statistics reduction (used by every de-dispersion kernel).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void chan_merge(double &n, double &m, double &q,
+                                           double n2, double m2, double q2)
+{
+    if (n2 == 0.0) return;
+    if (n == 0.0) { n = n2; m = m2; q = q2; return; }
+    double nn = n + n2;
+    double d = m2 - m;
+    m = m + d * (n2 / nn);
+    q = q + q2 + d * d * (n * n2 / nn);
+    n = nn;
+}
+
+// Reduce per-thread (n, mean, M2) over the block; thread 0 writes the result.
+__device__ void block_stat_f(double n, double m, double q, StatF *dst)
+{
+    __shared__ double sh[3][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        double n2 = __shfl_down_sync(0xffffffffu, n, off);
+        double m2 = __shfl_down_sync(0xffffffffu, m, off);
+        double q2 = __shfl_down_sync(0xffffffffu, q, off);
+        chan_merge(n, m, q, n2, m2, q2);
+    }
+    if (lane == 0) { sh[0][warp] = n; sh[1][warp] = m; sh[2][warp] = q; }
+    __syncthreads();
+    if (warp == 0) {
+        n = lane < nwarps ? sh[0][lane] : 0.0;
+        m = lane < nwarps ? sh[1][lane] : 0.0;
+        q = lane < nwarps ? sh[2][lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            double n2 = __shfl_down_sync(0xffffffffu, n, off);
+            double m2 = __shfl_down_sync(0xffffffffu, m, off);
+            double q2 = __shfl_down_sync(0xffffffffu, q, off);
+            chan_merge(n, m, q, n2, m2, q2);
+        }
+        if (lane == 0) { dst->n = n; dst->mean = m; dst->m2 = q; }
+    }
+}
+
+__device__ void block_stat_i(long long n, long long s, unsigned long long q, StatI *dst)
+{
+    __shared__ long long shn[32], shs[32];
+    __shared__ unsigned long long shq[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        n += __shfl_down_sync(0xffffffffu, n, off);
+        s += __shfl_down_sync(0xffffffffu, s, off);
+        q += __shfl_down_sync(0xffffffffu, q, off);
+    }
+    if (lane == 0) { shn[warp] = n; shs[warp] = s; shq[warp] = q; }
+    __syncthreads();
+    if (warp == 0) {
+        n = lane < nwarps ? shn[lane] : 0;
+        s = lane < nwarps ? shs[lane] : 0;
+        q = lane < nwarps ? shq[lane] : 0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            n += __shfl_down_sync(0xffffffffu, n, off);
+            s += __shfl_down_sync(0xffffffffu, s, off);
+            q += __shfl_down_sync(0xffffffffu, q, off);
+        }
+        if (lane == 0) { dst->n = n; dst->sum = s; dst->sumsq = q; }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel 1: generic shared-memory de-dispersion.
+//
+// Block = kGenDms DM trials x kGenTile samples.  For each stage of `chunk`
+// channels the block copies, per channel, the input span covering all its
+// DM trials ([t0 + base, t0 + base + kGenTile + span)) into shared memory,
+// converting to float; each thread then adds, for each of its samples and
+// DM trials, the element at its delay offset.  One shared load per add.
+// With chunk == 0 (span too large for shared memory) it reads global memory
+// directly.
+// ---------------------------------------------------------------------------
+template <typename Tin, bool kInt>
+__global__ void __launch_bounds__(kGenThreads)
+generic_kernel(const Tin *__restrict__ in, int64_t pitch, int64_t nsamp_in, int nchans,
+               const int32_t *__restrict__ goffs,   // [dmblk][nchans][kGenDms]
+               const int32_t *__restrict__ gbase,   // [dmblk][nchans]
+               const int32_t *__restrict__ gspan,   // [dmblk][nchans]
+               int ndm, int64_t nout, void *__restrict__ out_, void *__restrict__ partials,
+               int chunk, int stride)
+{
+    extern __shared__ float smem[];
+    const int tid = threadIdx.x;
+    const int64_t t0 = (int64_t)blockIdx.x * kGenTile;
+    const int blk = blockIdx.y;
+    const int dm0 = blk * kGenDms;
+    const int ndb = min(kGenDms, ndm - dm0);
+    const int32_t *boffs = goffs + (size_t)blk * nchans * kGenDms;
+    const int32_t *bbase = gbase + (size_t)blk * nchans;
+    const int32_t *bspan = gspan + (size_t)blk * nchans;
+
+    float acc[kGenDms][kGenTimes];
+#pragma unroll
+    for (int j = 0; j < kGenDms; ++j)
+#pragma unroll
+        for (int k = 0; k < kGenTimes; ++k) acc[j][k] = 0.f;
+
+    if (chunk > 0) {
+        float *rows = smem;
+        int *offs = reinterpret_cast<int *>(smem + (size_t)chunk * stride);
+        for (int c0 = 0; c0 < nchans; c0 += chunk) {
+            const int cn = min(chunk, nchans - c0);
+            __syncthreads();
+            for (int i = tid; i < cn * kGenDms; i += kGenThreads)
+                offs[i] = boffs[(size_t)c0 * kGenDms + i];
+            for (int c = 0; c < cn; ++c) {
+                const int64_t s0 = t0 + bbase[c0 + c];
+                const int len = kGenTile + bspan[c0 + c];
+                const Tin *src = in + (size_t)(c0 + c) * pitch;
+                float *dst = rows + (size_t)c * stride;
+                for (int i = tid; i < len; i += kGenThreads) {
+                    const int64_t s = s0 + i;
+                    dst[i] = (s < nsamp_in) ? to_f(src[s]) : 0.f;
+                }
+            }
+            __syncthreads();
+            for (int c = 0; c < cn; ++c) {
+                const float *r = rows + (size_t)c * stride + tid;
+                const int *o = offs + c * kGenDms;
+#pragma unroll
+                for (int j = 0; j < kGenDms; ++j) {
+                    const int oj = o[j];
+#pragma unroll
+                    for (int k = 0; k < kGenTimes; ++k) acc[j][k] += r[oj + k * kGenThreads];
+                }
+            }
+        }
+    } else {
+        for (int c = 0; c < nchans; ++c) {
+            const Tin *src = in + (size_t)c * pitch + bbase[c];
+            const int32_t *o = boffs + (size_t)c * kGenDms;
+#pragma unroll
+            for (int j = 0; j < kGenDms; ++j) {
+                const int oj = o[j];
+#pragma unroll
+                for (int k = 0; k < kGenTimes; ++k) {
+                    const int64_t s = t0 + tid + k * kGenThreads + oj;
+                    if (s + bbase[c] < nsamp_in) acc[j][k] += to_f(src[s]);
+                }
+            }
+        }
+    }
+
+    // Epilogue: store, then per-block partial statistics.
+    const int64_t pidx = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    if constexpr (kInt) {
+        int32_t *out = reinterpret_cast<int32_t *>(out_);
+        long long n = 0, s = 0;
+        unsigned long long q = 0;
+#pragma unroll
+        for (int j = 0; j < kGenDms; ++j)
+#pragma unroll
+            for (int k = 0; k < kGenTimes; ++k) {
+                const int64_t t = t0 + tid + k * kGenThreads;
+                if (j < ndb && t < nout) {
+                    const int v = __float2int_rn(acc[j][k]);
+                    out[(size_t)(dm0 + j) * nout + t] = v;
+                    n += 1; s += v; q += (unsigned long long)((long long)v * v);
+                }
+            }
+        block_stat_i(n, s, q, reinterpret_cast<StatI *>(partials) + pidx);
+    } else {
+        float *out = reinterpret_cast<float *>(out_);
+        int n = 0;
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < kGenDms; ++j)
+#pragma unroll
+            for (int k = 0; k < kGenTimes; ++k) {
+                const int64_t t = t0 + tid + k * kGenThreads;
+                if (j < ndb && t < nout) {
+                    out[(size_t)(dm0 + j) * nout + t] = acc[j][k];
+                    n += 1; s += acc[j][k];
+                }
+            }
+        const float m = n ? s / (float)n : 0.f;
+        float q = 0.f;
+#pragma unroll
+        for (int j = 0; j < kGenDms; ++j)
+#pragma unroll
+            for (int k = 0; k < kGenTimes; ++k) {
+                const int64_t t = t0 + tid + k * kGenThreads;
+                if (j < ndb && t < nout) { const float d = acc[j][k] - m; q += d * d; }
+            }
+        block_stat_f((double)n, (double)m, (double)q, reinterpret_cast<StatF *>(partials) + pidx);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Statistics straight from an `out` buffer (used when dd_search is given a
+// buffer other than the one the last dd_execute produced).
+// ---------------------------------------------------------------------------
+constexpr int kStatThreads = 256;
+constexpr int kStatPer = 16;   // elements per thread
+
+template <bool kInt>
+__global__ void __launch_bounds__(kStatThreads)
+stats_kernel(const void *__restrict__ out_, int64_t total, void *__restrict__ partials)
+{
+    const int64_t base = (int64_t)blockIdx.x * kStatThreads * kStatPer;
+    if constexpr (kInt) {
+        const int32_t *x = reinterpret_cast<const int32_t *>(out_);
+        long long n = 0, s = 0;
+        unsigned long long q = 0;
+        for (int k = 0; k < kStatPer; ++k) {
+            const int64_t i = base + (int64_t)k * kStatThreads + threadIdx.x;
+            if (i < total) { const long long v = x[i]; n++; s += v; q += (unsigned long long)(v * v); }
+        }
+        block_stat_i(n, s, q, reinterpret_cast<StatI *>(partials) + blockIdx.x);
+    } else {
+        const float *x = reinterpret_cast<const float *>(out_);
+        float v[kStatPer];
+        int n = 0;
+        float s = 0.f;
+        for (int k = 0; k < kStatPer; ++k) {
+            const int64_t i = base + (int64_t)k * kStatThreads + threadIdx.x;
+            v[k] = i < total ? x[i] : 0.f;
+            if (i < total) { n++; s += v[k]; }
+        }
+        const float m = n ? s / (float)n : 0.f;
+        float q = 0.f;
+        for (int k = 0; k < kStatPer; ++k) {
+            const int64_t i = base + (int64_t)k * kStatThreads + threadIdx.x;
+            if (i < total) { const float d = v[k] - m; q += d * d; }
+        }
+        block_stat_f((double)n, (double)m, (double)q, reinterpret_cast<StatF *>(partials) + blockIdx.x);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Finalise: merge the partials, form mu, sigma and the per-width thresholds
+// T_w = w*mu + k*sigma*sqrt(w) in double (Section 3's n-sigma test applied
+// to boxcar sums).  One block of 1024 threads.
+// ---------------------------------------------------------------------------
+constexpr int kFinThreads = 1024;
+
+template <bool kInt>
+__global__ void __launch_bounds__(kFinThreads)
+finalize_kernel(const void *__restrict__ partials, int64_t np, const int32_t *__restrict__ widths,
+                int nw, double k, SearchParams *__restrict__ prm)
+{
+    __shared__ double mu_s, sg_s;
+    if constexpr (kInt) {
+        __shared__ long long sn[kFinThreads], ss[kFinThreads];
+        __shared__ unsigned long long sq_lo[kFinThreads], sq_hi[kFinThreads];
+        const StatI *p = reinterpret_cast<const StatI *>(partials);
+        long long n = 0, s = 0;
+        unsigned __int128 q = 0;
+        for (int64_t i = threadIdx.x; i < np; i += kFinThreads) {
+            n += p[i].n; s += p[i].sum; q += (unsigned __int128)p[i].sumsq;
+        }
+        sn[threadIdx.x] = n; ss[threadIdx.x] = s;
+        sq_lo[threadIdx.x] = (unsigned long long)q;
+        sq_hi[threadIdx.x] = (unsigned long long)(q >> 64);
+        __syncthreads();
+        for (int h = kFinThreads / 2; h > 0; h >>= 1) {
+            if (threadIdx.x < h) {
+                const int o = threadIdx.x + h;
+                sn[threadIdx.x] += sn[o];
+                ss[threadIdx.x] += ss[o];
+                unsigned __int128 a = ((unsigned __int128)sq_hi[threadIdx.x] << 64) | sq_lo[threadIdx.x];
+                unsigned __int128 b = ((unsigned __int128)sq_hi[o] << 64) | sq_lo[o];
+                a += b;
+                sq_lo[threadIdx.x] = (unsigned long long)a;
+                sq_hi[threadIdx.x] = (unsigned long long)(a >> 64);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            const long long N = sn[0], S = ss[0];
+            const unsigned __int128 Q = ((unsigned __int128)sq_hi[0] << 64) | sq_lo[0];
+            // N*Q - S^2 >= 0 exactly (Cauchy-Schwarz), then one rounding each.
+            const __int128 num = (__int128)((unsigned __int128)N * Q) - (__int128)S * (__int128)S;
+            const double dn = (double)N;
+            mu_s = (double)S / dn;
+            sg_s = sqrt((double)num / (dn * dn));
+        }
+    } else {
+        __shared__ double sn[kFinThreads], sm[kFinThreads], sq[kFinThreads];
+        const StatF *p = reinterpret_cast<const StatF *>(partials);
+        double n = 0, m = 0, q = 0;
+        for (int64_t i = threadIdx.x; i < np; i += kFinThreads)
+            chan_merge(n, m, q, p[i].n, p[i].mean, p[i].m2);
+        sn[threadIdx.x] = n; sm[threadIdx.x] = m; sq[threadIdx.x] = q;
+        __syncthreads();
+        for (int h = kFinThreads / 2; h > 0; h >>= 1) {
+            if (threadIdx.x < h) {
+                double a = sn[threadIdx.x], b = sm[threadIdx.x], c = sq[threadIdx.x];
+                chan_merge(a, b, c, sn[threadIdx.x + h], sm[threadIdx.x + h], sq[threadIdx.x + h]);
+                sn[threadIdx.x] = a; sm[threadIdx.x] = b; sq[threadIdx.x] = c;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            mu_s = sm[0];
+            sg_s = sqrt(sq[0] / sn[0]);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) { prm->mu = mu_s; prm->sigma = sg_s; prm->nw = nw; }
+    if (threadIdx.x < nw) {
+        const double w = (double)widths[threadIdx.x];
+        const double T = w * mu_s + k * sg_s * sqrt(w);
+        prm->thr_f[threadIdx.x] = __double2float_rd(T);
+        double f = floor(T);
+        f = fmin(fmax(f, -4.0e18), 4.0e18);
+        prm->thr_i[threadIdx.x] = (long long)f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Boxcar threshold search.  Block = one DM row x kSearchTile samples; each
+// thread owns samples t = t0 + tid + kSearchThreads*k and extends a running
+// sum across the sorted widths, testing B_w > T_w at each requested width.
+// Hits are appended with one atomic each (hits are rare by construction).
+// ---------------------------------------------------------------------------
+constexpr int kSearchThreads = 256;
+constexpr int kSearchPer = 4;
+constexpr int kSearchTile = kSearchThreads * kSearchPer;
+
+template <bool kInt>
+__global__ void __launch_bounds__(kSearchThreads)
+search_kernel(const void *__restrict__ out_, int64_t nout,
+              const int32_t *__restrict__ wsorted, int nw, int wmax,
+              const SearchParams *__restrict__ prm, dd_candidate *__restrict__ cands,
+              int64_t cap, unsigned long long *__restrict__ count)
+{
+    extern __shared__ unsigned char sraw[];
+    __shared__ int sw[kMaxWidths], sidx[kMaxWidths];
+    __shared__ float thf[kMaxWidths];
+    __shared__ long long thi[kMaxWidths];
+    const int row = blockIdx.y;
+    const int64_t t0 = (int64_t)blockIdx.x * kSearchTile;
+    const int len = kSearchTile + wmax - 1;
+    if (threadIdx.x < nw) {
+        sw[threadIdx.x] = wsorted[threadIdx.x];
+        sidx[threadIdx.x] = wsorted[nw + threadIdx.x];
+        thf[threadIdx.x] = prm->thr_f[sidx[threadIdx.x]];
+        thi[threadIdx.x] = prm->thr_i[sidx[threadIdx.x]];
+    }
+    const double mu = prm->mu, sg = prm->sigma;
+    if constexpr (kInt) {
+        int32_t *x = reinterpret_cast<int32_t *>(sraw);
+        const int32_t *src = reinterpret_cast<const int32_t *>(out_) + (size_t)row * nout;
+        for (int i = threadIdx.x; i < len; i += kSearchThreads) {
+            const int64_t t = t0 + i;
+            x[i] = t < nout ? src[t] : 0;
+        }
+        __syncthreads();
+        for (int k = 0; k < kSearchPer; ++k) {
+            const int li = threadIdx.x + k * kSearchThreads;
+            const int64_t t = t0 + li;
+            if (t >= nout) break;
+            long long acc = 0;
+            int p = 0;
+            for (int j = 0; j < wmax && p < nw; ++j) {
+                if (t + j >= nout) break;
+                acc += x[li + j];
+                while (p < nw && sw[p] == j + 1) {
+                    if (acc > thi[p]) {
+                        const unsigned long long pos = atomicAdd(count, 1ull);
+                        if ((int64_t)pos < cap) {
+                            dd_candidate c;
+                            c.dm_idx = row; c.width_idx = sidx[p]; c.t = t;
+                            const double w = (double)(j + 1);
+                            c.snr = (float)(((double)acc - w * mu) / (sg * sqrt(w)));
+                            c.reserved = 0.f; c.value = (double)acc;
+                            cands[pos] = c;
+                        }
+                    }
+                    ++p;
+                }
+            }
+        }
+    } else {
+        float *x = reinterpret_cast<float *>(sraw);
+        const float *src = reinterpret_cast<const float *>(out_) + (size_t)row * nout;
+        for (int i = threadIdx.x; i < len; i += kSearchThreads) {
+            const int64_t t = t0 + i;
+            x[i] = t < nout ? src[t] : 0.f;
+        }
+        __syncthreads();
+        for (int k = 0; k < kSearchPer; ++k) {
+            const int li = threadIdx.x + k * kSearchThreads;
+            const int64_t t = t0 + li;
+            if (t >= nout) break;
+            float acc = 0.f;
+            int p = 0;
+            for (int j = 0; j < wmax && p < nw; ++j) {
+                if (t + j >= nout) break;
+                acc += x[li + j];
+                while (p < nw && sw[p] == j + 1) {
+                    if (acc > thf[p]) {
+                        const unsigned long long pos = atomicAdd(count, 1ull);
+                        if ((int64_t)pos < cap) {
+                            dd_candidate c;
+                            c.dm_idx = row; c.width_idx = sidx[p]; c.t = t;
+                            const double w = (double)(j + 1);
+                            c.snr = (float)(((double)acc - w * mu) / (sg * sqrt(w)));
+                            c.reserved = 0.f; c.value = (double)acc;
+                            cands[pos] = c;
+                        }
+                    }
+                    ++p;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+static size_t stat_size(const dd_plan *p)
+{
+    return p->dtype == DD_U8 ? sizeof(StatI) : sizeof(StatF);
+}
+
+static int ensure_partials(dd_plan *p, int64_t n)
+{
+    if (n <= p->n_partials_cap) return DD_OK;
+    if (p->d_partials) cudaFree(p->d_partials);
+    p->d_partials = nullptr;
+    p->n_partials_cap = 0;
+    cudaError_t e = cudaMalloc(&p->d_partials, (size_t)n * stat_size(p));
+    if (e != cudaSuccess) return set_error(DD_ERR_NOMEM, "cudaMalloc(partials, %lld): %s",
+                                           (long long)n, cudaGetErrorString(e));
+    p->n_partials_cap = n;
+    return DD_OK;
+}
+
+int generic_configure(dd_plan *p)
+{
+    const int nblk = (p->ndm + kGenDms - 1) / kGenDms;
+    const int C = p->nchans;
+    std::vector<int32_t> offs((size_t)nblk * C * kGenDms), base((size_t)nblk * C), span((size_t)nblk * C);
+    int maxspan = 0;
+    for (int b = 0; b < nblk; ++b) {
+        const int dm0 = b * kGenDms, ndb = std::min(kGenDms, p->ndm - dm0);
+        for (int c = 0; c < C; ++c) {
+            int lo = INT32_MAX, hi = INT32_MIN;
+            for (int j = 0; j < ndb; ++j) {
+                const int d = p->delays[(size_t)(dm0 + j) * C + c];
+                lo = std::min(lo, d); hi = std::max(hi, d);
+            }
+            base[(size_t)b * C + c] = lo;
+            span[(size_t)b * C + c] = hi - lo;
+            maxspan = std::max(maxspan, hi - lo);
+            for (int j = 0; j < kGenDms; ++j) {
+                const int jj = std::min(j, ndb - 1);
+                offs[((size_t)b * C + c) * kGenDms + j] = p->delays[(size_t)(dm0 + jj) * C + c] - lo;
+            }
+        }
+    }
+    // Shared-memory geometry: rows of kGenTile + maxspan floats (rounded to 4).
+    const int stride = ((kGenTile + maxspan + 3) / 4) * 4;
+    const size_t budget = std::min<size_t>(p->smem_optin, 100 * 1024);
+    const size_t per_chan = (size_t)stride * sizeof(float) + kGenDms * sizeof(int);
+    int chunk = (int)std::min<size_t>(16, budget / per_chan);
+    if (chunk < 1) chunk = 0;
+    p->gen_stride = stride;
+    p->gen_chunk = chunk;
+    p->gen_smem = chunk ? (size_t)chunk * per_chan : 0;
+
+    // Device copies, packed as [offs | base | span] in one allocation.
+    void *dptr = nullptr;
+    const size_t bytes = (offs.size() + base.size() + span.size()) * sizeof(int32_t);
+    cudaError_t e = cudaMalloc(&dptr, bytes);
+    if (e != cudaSuccess) return set_error(DD_ERR_NOMEM, "cudaMalloc(generic tables): %s", cudaGetErrorString(e));
+    int32_t *d = static_cast<int32_t *>(dptr);
+    e = cudaMemcpy(d, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + offs.size(), base.data(), base.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d + offs.size() + base.size(), span.data(), span.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { cudaFree(dptr); return cuda_fail(e, "upload generic tables"); }
+    p->d_gen = d;
+    if (chunk) {
+        auto set = [&](const void *fn) {
+            return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->gen_smem);
+        };
+        cudaError_t a = cudaSuccess;
+        a = set((const void *)generic_kernel<float, false>);
+        if (a == cudaSuccess) a = set((const void *)generic_kernel<__half, false>);
+        if (a == cudaSuccess) a = set((const void *)generic_kernel<uint8_t, true>);
+        if (a != cudaSuccess) return cuda_fail(a, "cudaFuncSetAttribute(generic)");
+    }
+    return DD_OK;
+}
+
+int generic_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStream_t s)
+{
+    const int nblk = (p->ndm + kGenDms - 1) / kGenDms;
+    const int64_t ntile = (p->nsamp_out + kGenTile - 1) / kGenTile;
+    if (ntile > INT32_MAX || nblk > 65535) return set_error(DD_ERR_ARG, "problem too large for kernel 1 grid");
+    const int64_t np = ntile * nblk;
+    int rc = ensure_partials(p, np);
+    if (rc) return rc;
+    const size_t noffs = (size_t)nblk * p->nchans * kGenDms;
+    const int32_t *goffs = p->d_gen;
+    const int32_t *gbase = goffs + noffs;
+    const int32_t *gspan = gbase + (size_t)nblk * p->nchans;
+    dim3 grid((unsigned)ntile, (unsigned)nblk);
+    switch (p->dtype) {
+    case DD_F32:
+        generic_kernel<float, false><<<grid, kGenThreads, p->gen_smem, s>>>(
+            (const float *)in, pitch, p->nsamp_in, p->nchans, goffs, gbase, gspan, p->ndm,
+            p->nsamp_out, out, p->d_partials, p->gen_chunk, p->gen_stride);
+        break;
+    case DD_F16:
+        generic_kernel<__half, false><<<grid, kGenThreads, p->gen_smem, s>>>(
+            (const __half *)in, pitch, p->nsamp_in, p->nchans, goffs, gbase, gspan, p->ndm,
+            p->nsamp_out, out, p->d_partials, p->gen_chunk, p->gen_stride);
+        break;
+    case DD_U8:
+        generic_kernel<uint8_t, true><<<grid, kGenThreads, p->gen_smem, s>>>(
+            (const uint8_t *)in, pitch, p->nsamp_in, p->nchans, goffs, gbase, gspan, p->ndm,
+            p->nsamp_out, out, p->d_partials, p->gen_chunk, p->gen_stride);
+        break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch generic_kernel");
+    p->n_partials = np;
+    p->stats_out = out;
+    return DD_OK;
+}
+
+int stats_from_out(dd_plan *p, const void *out, cudaStream_t s)
+{
+    const int64_t total = (int64_t)p->ndm * p->nsamp_out;
+    const int64_t per = (int64_t)kStatThreads * kStatPer;
+    const int64_t nb = (total + per - 1) / per;
+    if (nb > INT32_MAX) return set_error(DD_ERR_ARG, "buffer too large for the stats kernel");
+    int rc = ensure_partials(p, nb);
+    if (rc) return rc;
+    if (p->dtype == DD_U8)
+        stats_kernel<true><<<(unsigned)nb, kStatThreads, 0, s>>>(out, total, p->d_partials);
+    else
+        stats_kernel<false><<<(unsigned)nb, kStatThreads, 0, s>>>(out, total, p->d_partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch stats_kernel");
+    p->n_partials = nb;
+    p->stats_out = out;
+    return DD_OK;
+}
+
+int search_launch(dd_plan *p, const void *out, cudaStream_t s)
+{
+    const bool isint = p->dtype == DD_U8;
+    // widths are stored original-order in [0,nw) of d_wsorted's tail region
+    const int32_t *w_orig = p->d_wsorted + 2 * p->nwidths;
+    if (isint)
+        finalize_kernel<true><<<1, kFinThreads, 0, s>>>(p->d_partials, p->n_partials, w_orig,
+                                                        p->nwidths, p->sigma_k, p->d_params);
+    else
+        finalize_kernel<false><<<1, kFinThreads, 0, s>>>(p->d_partials, p->n_partials, w_orig,
+                                                         p->nwidths, p->sigma_k, p->d_params);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch finalize_kernel");
+    e = cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "memset count");
+    int wmax = 0;
+    for (int w : p->widths) wmax = std::max(wmax, w);
+    const int64_t ntile = (p->nsamp_out + kSearchTile - 1) / kSearchTile;
+    dim3 grid((unsigned)ntile, (unsigned)p->ndm);
+    const size_t smem = (size_t)(kSearchTile + wmax - 1) * 4;
+    if (isint)
+        search_kernel<true><<<grid, kSearchThreads, smem, s>>>(out, p->nsamp_out, p->d_wsorted, p->nwidths,
+                                                               wmax, p->d_params, p->d_cands, p->cand_cap, p->d_count);
+    else
+        search_kernel<false><<<grid, kSearchThreads, smem, s>>>(out, p->nsamp_out, p->d_wsorted, p->nwidths,
+                                                                wmax, p->d_params, p->d_cands, p->cand_cap, p->d_count);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch search_kernel");
+    return DD_OK;
+}
+
+}  // namespace dd

@@ -1,0 +1,231 @@
+"""ctypes binding of libdd (include/dd.h): argument marshalling only.
+
+Every step of de-dispersion and search runs in the CUDA kernels of libdd.so;
+this module converts Python/numpy/torch arguments to the C ABI and raises on
+any non-zero status.  There is no CPU fallback: if libdd.so is missing or
+cannot be loaded, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdd.so")
+
+DD_F32, DD_U8, DD_F16 = 0, 1, 2
+DD_OK, DD_ERR_ARG, DD_ERR_NOMEM, DD_ERR_CUDA, DD_ERR_OVERFLOW, DD_ERR_TIMEOUT, DD_ERR_BUDGET = range(7)
+
+CANDIDATE_DTYPE = np.dtype([("dm_idx", np.int32), ("width_idx", np.int32), ("t", np.int64),
+                            ("snr", np.float32), ("reserved", np.float32), ("value", np.float64)])
+assert CANDIDATE_DTYPE.itemsize == 32
+
+# Names of every function declared in include/dd.h.
+EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "dd_search",
+           "dd_last_stats", "dd_process_host", "dd_plan_set_kernel", "dd_plan_get_kernel",
+           "dd_last_error", "dd_version")
+
+
+class DDError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libdd status {code}: {msg}")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load libdd.so (once) and declare the C signatures."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libdd.so not found at {p}: build it with "
+                               "paper_1107_2516_gb300.build.build() (nvcc, sm_103a)")
+        lib = C.CDLL(p)
+        vp, i32, i64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        P64 = C.POINTER(C.c_int64)
+        sig = {
+            "dd_plan_create": (C.c_int, [i32, f64, f64, f64, vp, i32, vp, i32, f64, i32, i64,
+                                         C.POINTER(vp)]),
+            "dd_plan_destroy": (C.c_int, [vp]),
+            "dd_plan_info": (C.c_int, [vp, P64, P64, vp]),
+            "dd_execute": (C.c_int, [vp, vp, i64, vp, vp]),
+            "dd_search": (C.c_int, [vp, vp, vp, i64, P64, vp]),
+            "dd_last_stats": (C.c_int, [vp, C.POINTER(f64), C.POINTER(f64)]),
+            "dd_process_host": (C.c_int, [vp, vp, i64, vp, i64, P64, vp]),
+            "dd_plan_set_kernel": (C.c_int, [vp, i32]),
+            "dd_plan_get_kernel": (C.c_int, [vp, C.POINTER(i32)]),
+            "dd_last_error": (C.c_char_p, []),
+            "dd_version": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype, f.argtypes = res, args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(rc: int, allow=()):
+    if rc != DD_OK and rc not in allow:
+        raise DDError(rc, load().dd_last_error().decode())
+    return rc
+
+
+def _ptr(x) -> int:
+    """Raw address of a torch tensor / numpy array / int."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return 0
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------ C-named calls
+
+def dd_version() -> str:
+    return load().dd_version().decode()
+
+
+def dd_last_error() -> str:
+    return load().dd_last_error().decode()
+
+
+def dd_plan_create(nchans: int, fch1: float, foff: float, tsamp: float, dm_list: Sequence[float],
+                   boxcar_widths: Sequence[int], sigma: float, in_dtype: int, nsamp_in: int) -> int:
+    dm = np.ascontiguousarray(np.asarray(dm_list, dtype=np.float64))
+    w = np.ascontiguousarray(np.asarray(boxcar_widths, dtype=np.int32))
+    out = C.c_void_p()
+    _check(load().dd_plan_create(int(nchans), float(fch1), float(foff), float(tsamp),
+                                 dm.ctypes.data, int(dm.size), w.ctypes.data, int(w.size),
+                                 float(sigma), int(in_dtype), int(nsamp_in), C.byref(out)))
+    return int(out.value)
+
+
+def dd_plan_destroy(plan: int) -> None:
+    _check(load().dd_plan_destroy(plan))
+
+
+def dd_plan_info(plan: int, ndm: int = 0, nchans: int = 0, delays: bool = False):
+    m, n = C.c_int64(), C.c_int64()
+    tab = np.empty((ndm, nchans), np.int32) if delays else None
+    _check(load().dd_plan_info(plan, C.byref(m), C.byref(n), _ptr(tab) if delays else None))
+    return (int(m.value), int(n.value), tab) if delays else (int(m.value), int(n.value))
+
+
+def dd_execute(plan: int, in_dev, in_pitch: int, out_dev, stream=None) -> None:
+    _check(load().dd_execute(plan, _ptr(in_dev), int(in_pitch), _ptr(out_dev), _stream(stream)))
+
+
+def dd_search(plan: int, out_dev, capacity: int = 1 << 16, stream=None, allow_overflow=False):
+    """Returns (candidates structured array sorted by (dm, t, width), true count)."""
+    cands = np.zeros(max(capacity, 1), dtype=CANDIDATE_DTYPE)
+    n = C.c_int64()
+    rc = _check(load().dd_search(plan, _ptr(out_dev), cands.ctypes.data, int(capacity), C.byref(n),
+                                 _stream(stream)), allow=(DD_ERR_OVERFLOW,) if allow_overflow else ())
+    total = int(n.value)
+    return cands[:min(total, capacity)].copy(), total
+
+
+def dd_last_stats(plan: int):
+    mu, sg = C.c_double(), C.c_double()
+    _check(load().dd_last_stats(plan, C.byref(mu), C.byref(sg)))
+    return float(mu.value), float(sg.value)
+
+
+def dd_process_host(plan: int, in_host, in_pitch: int, capacity: int = 1 << 16, stream=None,
+                    allow_overflow=False):
+    cands = np.zeros(max(capacity, 1), dtype=CANDIDATE_DTYPE)
+    n = C.c_int64()
+    _check(load().dd_process_host(plan, _ptr(in_host), int(in_pitch), cands.ctypes.data,
+                                  int(capacity), C.byref(n), _stream(stream)),
+           allow=(DD_ERR_OVERFLOW,) if allow_overflow else ())
+    total = int(n.value)
+    return cands[:min(total, capacity)].copy(), total
+
+
+def dd_plan_set_kernel(plan: int, kernel: int) -> None:
+    _check(load().dd_plan_set_kernel(plan, int(kernel)))
+
+
+def dd_plan_get_kernel(plan: int) -> int:
+    k = C.c_int32()
+    _check(load().dd_plan_get_kernel(plan, C.byref(k)))
+    return int(k.value)
+
+
+# ------------------------------------------------------------- convenience object
+
+class Plan:
+    """Owning wrapper around a dd_plan handle (marshalling only)."""
+
+    def __init__(self, nchans, fch1, foff, tsamp, dm_list, boxcar_widths, sigma, in_dtype, nsamp_in):
+        self.nchans, self.ndm = int(nchans), len(dm_list)
+        self.in_dtype = int(in_dtype)
+        self.handle = dd_plan_create(nchans, fch1, foff, tsamp, dm_list, boxcar_widths, sigma,
+                                     in_dtype, nsamp_in)
+        self.maxshift, self.nsamp_out = dd_plan_info(self.handle)
+
+    @property
+    def out_is_int(self) -> bool:
+        return self.in_dtype == DD_U8
+
+    def delays(self) -> np.ndarray:
+        return dd_plan_info(self.handle, self.ndm, self.nchans, delays=True)[2]
+
+    def execute(self, in_dev, in_pitch, out_dev, stream=None):
+        dd_execute(self.handle, in_dev, in_pitch, out_dev, stream)
+
+    def search(self, out_dev, capacity=1 << 16, stream=None, allow_overflow=False):
+        return dd_search(self.handle, out_dev, capacity, stream, allow_overflow)
+
+    def stats(self):
+        return dd_last_stats(self.handle)
+
+    def process_host(self, in_host, in_pitch, capacity=1 << 16, stream=None, allow_overflow=False):
+        return dd_process_host(self.handle, in_host, in_pitch, capacity, stream, allow_overflow)
+
+    def set_kernel(self, k):
+        dd_plan_set_kernel(self.handle, k)
+
+    @property
+    def kernel(self):
+        return dd_plan_get_kernel(self.handle)
+
+    def close(self):
+        if self.handle:
+            dd_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

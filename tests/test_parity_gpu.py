@@ -1,0 +1,170 @@
+"""GPU parity: libdd (through its C ABI) against the CPU oracle.
+
+Criteria: delay tables bit-equal; uint8 -> int32 output bit-exact; FP32 and
+FP16 -> FP32 output within 1e-5 * nchans (unit-variance data); mu/sigma
+consistent; candidate lists identical outside the gray zone (points whose
+oracle boxcar lies within the FP error bound of the threshold).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from ddhelpers import compare_candidates, fp_tol, keys, make_input
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1107_2516_gb300 as dd
+from paper_1107_2516_gb300 import build as ddbuild
+
+DTYPES = {"f32": dd.DD_F32, "u8": dd.DD_U8, "f16": dd.DD_F16}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ddbuild.build()
+    dd.load()
+
+
+def to_device(arr: np.ndarray):
+    if arr.dtype == np.uint16:
+        arr = arr.view(np.int16)
+    return torch.from_numpy(np.ascontiguousarray(arr)).cuda()
+
+
+def run_case(nchans, fch1, foff, tsamp, nsamp, dm_list, widths, sigma, dtype="f32", seed=0,
+             pulses=(), pitch=None, kernel=0, check_cands=True, max_gray=0):
+    arr, _ = make_input(nchans, nsamp, fch1, foff, tsamp, seed, pulses, dtype, pitch)
+    pitch = arr.shape[1]
+    plan = dd.Plan(nchans, fch1, foff, tsamp, dm_list, widths, sigma, DTYPES[dtype], nsamp)
+    if kernel:
+        plan.set_kernel(kernel)
+    d_o, m_o = oracle.delays(nchans, fch1, foff, tsamp, dm_list)
+    assert plan.maxshift == m_o
+    assert np.array_equal(plan.delays().astype(np.int64), d_o)
+    nout = nsamp - m_o
+    assert plan.nsamp_out == nout
+    in_dev = to_device(arr)
+    out_dev = torch.empty(len(dm_list) * nout, dtype=torch.int32 if dtype == "u8" else torch.float32,
+                          device="cuda")
+    plan.execute(in_dev, pitch, out_dev)
+    cands, total = plan.search(out_dev, capacity=1 << 18)
+    torch.cuda.synchronize()
+    out = out_dev.cpu().numpy().reshape(len(dm_list), nout)
+    ora = oracle.dedisperse(arr, d_o, nout)
+    if dtype == "u8":
+        assert np.array_equal(out.astype(np.int64), ora)
+    else:
+        err = np.max(np.abs(out.astype(np.float64) - ora))
+        assert err <= fp_tol(nchans), err
+    mu_g, sg_g = plan.stats()
+    mu_o, sg_o = oracle.stats(ora)
+    if dtype == "u8":
+        assert abs(mu_g - mu_o) <= 1e-12 * max(1.0, abs(mu_o))
+        assert abs(sg_g - sg_o) <= 1e-12 * max(1.0, sg_o)
+    else:
+        assert abs(mu_g - mu_o) <= fp_tol(nchans)
+        assert abs(sg_g - sg_o) <= 1e-5 * max(1.0, sg_o)
+    assert total == len(cands)
+    res = None
+    if check_cands:
+        eps = 0.0 if dtype == "u8" else fp_tol(nchans)
+        res = compare_candidates(cands, ora, list(widths), mu_g, sg_g, mu_o, sg_o, sigma, eps)
+        assert res[1] <= max_gray, f"{res[1]} gray-zone points"
+    plan.close()
+    return cands, out, ora, res
+
+
+SMALL = synth.workload("small_f32")
+
+
+def small_pulse():
+    return [synth.Pulse(dm=float(SMALL.dm_list[30]), t0=4000, width=4, amp=5.0)]
+
+
+@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("dtype", ["f32", "u8", "f16"])
+def test_small_workload_parity(dtype, kernel):
+    wl = SMALL
+    cands, out, ora, res = run_case(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.nsamp, wl.dm_list,
+                                    wl.widths, wl.sigma, dtype, seed=wl.seed, pulses=small_pulse(),
+                                    kernel=kernel)
+    best = cands[np.argmax(cands["snr"])]
+    assert (int(best["dm_idx"]), int(best["t"]), int(best["width_idx"])) == (30, 4000, 2)
+
+
+EDGE = [
+    # nchans, nsamp extra beyond maxshift, dm_list, widths, pitch_pad, foff sign
+    (1, 1, [0.0], [1], 0, -1),
+    (3, 31, [0.0, 1.0, 2.0], [1, 2], 0, -1),
+    (3, 32, [0.0, 1.0, 2.0], [1, 32], 0, -1),
+    (128, 33, [0.5 * i for i in range(17)], [1, 2, 4, 8], 1, -1),
+    (128, 1000, [0.0] * 5, [1, 3, 7], 0, -1),                       # maxshift 0
+    (64, 777, [3.1, 0.2, 5.5, 1.0, 0.0, 2.2], [2, 1, 4], 3, -1),    # unsorted DMs
+    (96, 600, [0.25 * i for i in range(40)], [1, 2, 4, 8, 16], 0, 1),  # ascending band
+    (200, 2049, [0.1 * i for i in range(33)], [1, 5], 5, -1),
+]
+
+
+@pytest.mark.parametrize("case", range(len(EDGE)))
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_edge_shapes(case, dtype):
+    nch, extra, dms, widths, pad, sgn = EDGE[case]
+    foff = sgn * 0.1953125
+    fch1 = 150.0 if sgn < 0 else 150.0 - (nch - 1) * 0.1953125
+    tsamp = 327.68e-6
+    _, m = oracle.delays(nch, fch1, foff, tsamp, dms)
+    nsamp = m + extra
+    pitch = nsamp + pad
+    for kernel in (0, 1):
+        run_case(nch, fch1, foff, tsamp, nsamp, dms, widths, 3.0, dtype, seed=case + 100,
+                 pitch=pitch, kernel=kernel, max_gray=2)
+
+
+def test_constant_input_gives_nchans_times_value():
+    # Section 4: "all the elements initialized to the same value"
+    nch, nsamp = 256, 4096
+    dms = [0.2 * i for i in range(24)]
+    plan = dd.Plan(nch, 150.0, -0.1953125, 327.68e-6, dms, [1, 2], 6.0, dd.DD_F32, nsamp)
+    x = torch.full((nch, nsamp), 0.75, dtype=torch.float32, device="cuda")
+    out = torch.empty(len(dms) * plan.nsamp_out, dtype=torch.float32, device="cuda")
+    plan.execute(x, nsamp, out)
+    torch.cuda.synchronize()
+    assert bool(torch.all(out == nch * 0.75))
+    plan.close()
+
+
+def test_search_overflow_reports_true_count():
+    wl = SMALL
+    arr, _ = make_input(wl.nchans, wl.nsamp, wl.fch1, wl.foff, wl.tsamp, 5)
+    plan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, 1.0, dd.DD_F32,
+                   wl.nsamp)
+    out = torch.empty(wl.ndm * plan.nsamp_out, dtype=torch.float32, device="cuda")
+    plan.execute(to_device(arr), wl.nsamp, out)
+    cands, total = plan.search(out, capacity=100, allow_overflow=True)
+    assert total > 100 and len(cands) == 100
+    k = [(int(r["dm_idx"]), int(r["t"]), int(r["width_idx"])) for r in cands]
+    assert k == sorted(k)
+    with pytest.raises(dd.DDError) as e:
+        plan.search(out, capacity=100)
+    assert e.value.code == dd.dd.DD_ERR_OVERFLOW
+    plan.close()
+
+
+def test_process_host_matches_device_path():
+    wl = SMALL
+    arr, _ = make_input(wl.nchans, wl.nsamp, wl.fch1, wl.foff, wl.tsamp, wl.seed, small_pulse())
+    plan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, wl.sigma,
+                   dd.DD_F32, wl.nsamp)
+    host = torch.from_numpy(arr).pin_memory()
+    c1, n1 = plan.process_host(host, wl.nsamp)
+    out = torch.empty(wl.ndm * plan.nsamp_out, dtype=torch.float32, device="cuda")
+    plan.execute(to_device(arr), wl.nsamp, out)
+    c2, n2 = plan.search(out)
+    assert n1 == n2 and keys(c1) == keys(c2)
+    plan.close()
