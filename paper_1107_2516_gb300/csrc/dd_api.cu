@@ -262,6 +262,8 @@ int dd_search(dd_plan *plan, const void *out_dev, dd_candidate *cand_host, int64
         e = cudaMemcpyAsync(plan->h_params, plan->d_params, sizeof(SearchParams), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "search readback");
+    rc = fast_error(plan, s);
+    if (rc) return rc;
     const int64_t total = (int64_t)*plan->h_count;
     const int64_t n = std::min<int64_t>(total, capacity);
     plan->last_mu = plan->h_params->mu;

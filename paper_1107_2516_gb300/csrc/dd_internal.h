@@ -98,10 +98,12 @@ int generic_configure(dd_plan *p);
 int generic_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStream_t s);
 int stats_from_out(dd_plan *p, const void *out, cudaStream_t s);
 int search_launch(dd_plan *p, const void *out, cudaStream_t s);
+int ensure_partials_public(dd_plan *p, int64_t n);
 
 // dd_fast.cu
 int fast_configure(dd_plan *p);
 int fast_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStream_t s);
 void fast_release(dd_plan *p);
+int fast_error(dd_plan *p, cudaStream_t s);
 
 }  // namespace dd

@@ -5,89 +5,13 @@
 // Section 3 (output stage): mean and standard deviation over the whole
 // processed buffer, an n-sigma threshold, every point above it reported.
 #include "dd_internal.h"
+#include "dd_device.cuh"
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 namespace dd {
-
-template <typename T> __device__ __forceinline__ float to_f(T v);
-template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
-template <> __device__ __forceinline__ float to_f<uint8_t>(uint8_t v) { return (float)v; }
-template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
-
-// ---------------------------------------------------------------------------
-// Block-level statistics reduction (used by every de-dispersion kernel).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void chan_merge(double &n, double &m, double &q,
-                                           double n2, double m2, double q2)
-{
-    if (n2 == 0.0) return;
-    if (n == 0.0) { n = n2; m = m2; q = q2; return; }
-    double nn = n + n2;
-    double d = m2 - m;
-    m = m + d * (n2 / nn);
-    q = q + q2 + d * d * (n * n2 / nn);
-    n = nn;
-}
-
-// Reduce per-thread (n, mean, M2) over the block; thread 0 writes the result.
-__device__ void block_stat_f(double n, double m, double q, StatF *dst)
-{
-    __shared__ double sh[3][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        double n2 = __shfl_down_sync(0xffffffffu, n, off);
-        double m2 = __shfl_down_sync(0xffffffffu, m, off);
-        double q2 = __shfl_down_sync(0xffffffffu, q, off);
-        chan_merge(n, m, q, n2, m2, q2);
-    }
-    if (lane == 0) { sh[0][warp] = n; sh[1][warp] = m; sh[2][warp] = q; }
-    __syncthreads();
-    if (warp == 0) {
-        n = lane < nwarps ? sh[0][lane] : 0.0;
-        m = lane < nwarps ? sh[1][lane] : 0.0;
-        q = lane < nwarps ? sh[2][lane] : 0.0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            double n2 = __shfl_down_sync(0xffffffffu, n, off);
-            double m2 = __shfl_down_sync(0xffffffffu, m, off);
-            double q2 = __shfl_down_sync(0xffffffffu, q, off);
-            chan_merge(n, m, q, n2, m2, q2);
-        }
-        if (lane == 0) { dst->n = n; dst->mean = m; dst->m2 = q; }
-    }
-}
-
-__device__ void block_stat_i(long long n, long long s, unsigned long long q, StatI *dst)
-{
-    __shared__ long long shn[32], shs[32];
-    __shared__ unsigned long long shq[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nwarps = (blockDim.x + 31) >> 5;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        n += __shfl_down_sync(0xffffffffu, n, off);
-        s += __shfl_down_sync(0xffffffffu, s, off);
-        q += __shfl_down_sync(0xffffffffu, q, off);
-    }
-    if (lane == 0) { shn[warp] = n; shs[warp] = s; shq[warp] = q; }
-    __syncthreads();
-    if (warp == 0) {
-        n = lane < nwarps ? shn[lane] : 0;
-        s = lane < nwarps ? shs[lane] : 0;
-        q = lane < nwarps ? shq[lane] : 0;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            n += __shfl_down_sync(0xffffffffu, n, off);
-            s += __shfl_down_sync(0xffffffffu, s, off);
-            q += __shfl_down_sync(0xffffffffu, q, off);
-        }
-        if (lane == 0) { dst->n = n; dst->sum = s; dst->sumsq = q; }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Kernel 1: generic shared-memory de-dispersion.
@@ -212,7 +136,7 @@ generic_kernel(const Tin *__restrict__ in, int64_t pitch, int64_t nsamp_in, int 
                 const int64_t t = t0 + tid + k * kGenThreads;
                 if (j < ndb && t < nout) { const float d = acc[j][k] - m; q += d * d; }
             }
-        block_stat_f((double)n, (double)m, (double)q, reinterpret_cast<StatF *>(partials) + pidx);
+        block_stat_f32(n, s, q, reinterpret_cast<StatF *>(partials) + pidx);
     }
 }
 
@@ -253,14 +177,18 @@ stats_kernel(const void *__restrict__ out_, int64_t total, void *__restrict__ pa
             const int64_t i = base + (int64_t)k * kStatThreads + threadIdx.x;
             if (i < total) { const float d = v[k] - m; q += d * d; }
         }
-        block_stat_f((double)n, (double)m, (double)q, reinterpret_cast<StatF *>(partials) + blockIdx.x);
+        block_stat_f32(n, s, q, reinterpret_cast<StatF *>(partials) + blockIdx.x);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Finalise: merge the partials, form mu, sigma and the per-width thresholds
-// T_w = w*mu + k*sigma*sqrt(w) in double (Section 3's n-sigma test applied
-// to boxcar sums).  One block of 1024 threads.
+// Finalise: merge the per-block partials into mu and sigma (population, over
+// the whole buffer) and form the per-width thresholds
+//   T_w = w*mu + k*sigma*sqrt(w)
+// in double (Section 3's n-sigma test applied to boxcar sums).  Each
+// threshold is stored as the largest float <= T_w and as floor(T_w), so the
+// kernels' FP32 / integer comparisons decide B_w > T_w exactly as a double
+// comparison of the same B_w would.  One block of 1024 threads.
 // ---------------------------------------------------------------------------
 constexpr int kFinThreads = 1024;
 
@@ -306,25 +234,33 @@ finalize_kernel(const void *__restrict__ partials, int64_t np, const int32_t *__
             sg_s = sqrt((double)num / (dn * dn));
         }
     } else {
-        __shared__ double sn[kFinThreads], sm[kFinThreads], sq[kFinThreads];
+        // Two passes over the partials, no division per partial:
+        //   mean = sum n_b*mean_b / N,  M2 = sum [M2_b + n_b*(mean_b - mean)^2].
+        __shared__ double sa[kFinThreads], sb[kFinThreads];
         const StatF *p = reinterpret_cast<const StatF *>(partials);
-        double n = 0, m = 0, q = 0;
-        for (int64_t i = threadIdx.x; i < np; i += kFinThreads)
-            chan_merge(n, m, q, p[i].n, p[i].mean, p[i].m2);
-        sn[threadIdx.x] = n; sm[threadIdx.x] = m; sq[threadIdx.x] = q;
+        double n = 0, s = 0;
+        for (int64_t i = threadIdx.x; i < np; i += kFinThreads) { n += p[i].n; s += p[i].n * p[i].mean; }
+        sa[threadIdx.x] = n; sb[threadIdx.x] = s;
         __syncthreads();
         for (int h = kFinThreads / 2; h > 0; h >>= 1) {
-            if (threadIdx.x < h) {
-                double a = sn[threadIdx.x], b = sm[threadIdx.x], c = sq[threadIdx.x];
-                chan_merge(a, b, c, sn[threadIdx.x + h], sm[threadIdx.x + h], sq[threadIdx.x + h]);
-                sn[threadIdx.x] = a; sm[threadIdx.x] = b; sq[threadIdx.x] = c;
-            }
+            if (threadIdx.x < h) { sa[threadIdx.x] += sa[threadIdx.x + h]; sb[threadIdx.x] += sb[threadIdx.x + h]; }
             __syncthreads();
         }
-        if (threadIdx.x == 0) {
-            mu_s = sm[0];
-            sg_s = sqrt(sq[0] / sn[0]);
+        const double N = sa[0];
+        const double M = N > 0 ? sb[0] / N : 0.0;
+        __syncthreads();
+        double q = 0;
+        for (int64_t i = threadIdx.x; i < np; i += kFinThreads) {
+            const double e = p[i].mean - M;
+            q += p[i].m2 + p[i].n * e * e;
         }
+        sa[threadIdx.x] = q;
+        __syncthreads();
+        for (int h = kFinThreads / 2; h > 0; h >>= 1) {
+            if (threadIdx.x < h) sa[threadIdx.x] += sa[threadIdx.x + h];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) { mu_s = M; sg_s = sqrt(sa[0] / N); }
     }
     __syncthreads();
     if (threadIdx.x == 0) { prm->mu = mu_s; prm->sigma = sg_s; prm->nw = nw; }
@@ -339,14 +275,20 @@ finalize_kernel(const void *__restrict__ partials, int64_t np, const int32_t *__
 }
 
 // ---------------------------------------------------------------------------
-// Boxcar threshold search.  Block = one DM row x kSearchTile samples; each
-// thread owns samples t = t0 + tid + kSearchThreads*k and extends a running
-// sum across the sorted widths, testing B_w > T_w at each requested width.
-// Hits are appended with one atomic each (hits are rare by construction).
+// Boxcar threshold search.  Block = one DM row x kSearchTile samples; thread
+// owns kSearchPer consecutive samples.  For the widths in ascending order it
+// extends B_w at its first sample from the previous width's sum, then slides
+// it along its samples (B_w(t+1) = B_w(t) + x[t+w] - x[t]), testing
+// B_w > T_w at each (t, w).  Only FP32 (or integer) arithmetic runs here;
+// hits are appended with one atomic each and their S/N is formed afterwards
+// by cand_snr_kernel.  The shared tile is padded one word per 16 so the
+// per-thread windows fall in distinct banks.
 // ---------------------------------------------------------------------------
 constexpr int kSearchThreads = 256;
-constexpr int kSearchPer = 4;
+constexpr int kSearchPer = 16;
 constexpr int kSearchTile = kSearchThreads * kSearchPer;
+
+__host__ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
 
 template <bool kInt>
 __global__ void __launch_bounds__(kSearchThreads)
@@ -355,10 +297,13 @@ search_kernel(const void *__restrict__ out_, int64_t nout,
               const SearchParams *__restrict__ prm, dd_candidate *__restrict__ cands,
               int64_t cap, unsigned long long *__restrict__ count)
 {
-    extern __shared__ unsigned char sraw[];
+    using T = typename std::conditional<kInt, int32_t, float>::type;
+    using Acc = typename std::conditional<kInt, long long, float>::type;
+    extern __shared__ __align__(16) unsigned char sraw[];
     __shared__ int sw[kMaxWidths], sidx[kMaxWidths];
     __shared__ float thf[kMaxWidths];
     __shared__ long long thi[kMaxWidths];
+    T *x = reinterpret_cast<T *>(sraw);
     const int row = blockIdx.y;
     const int64_t t0 = (int64_t)blockIdx.x * kSearchTile;
     const int len = kSearchTile + wmax - 1;
@@ -368,73 +313,50 @@ search_kernel(const void *__restrict__ out_, int64_t nout,
         thf[threadIdx.x] = prm->thr_f[sidx[threadIdx.x]];
         thi[threadIdx.x] = prm->thr_i[sidx[threadIdx.x]];
     }
-    const double mu = prm->mu, sg = prm->sigma;
-    if constexpr (kInt) {
-        int32_t *x = reinterpret_cast<int32_t *>(sraw);
-        const int32_t *src = reinterpret_cast<const int32_t *>(out_) + (size_t)row * nout;
-        for (int i = threadIdx.x; i < len; i += kSearchThreads) {
-            const int64_t t = t0 + i;
-            x[i] = t < nout ? src[t] : 0;
-        }
-        __syncthreads();
-        for (int k = 0; k < kSearchPer; ++k) {
-            const int li = threadIdx.x + k * kSearchThreads;
-            const int64_t t = t0 + li;
-            if (t >= nout) break;
-            long long acc = 0;
-            int p = 0;
-            for (int j = 0; j < wmax && p < nw; ++j) {
-                if (t + j >= nout) break;
-                acc += x[li + j];
-                while (p < nw && sw[p] == j + 1) {
-                    if (acc > thi[p]) {
-                        const unsigned long long pos = atomicAdd(count, 1ull);
-                        if ((int64_t)pos < cap) {
-                            dd_candidate c;
-                            c.dm_idx = row; c.width_idx = sidx[p]; c.t = t;
-                            const double w = (double)(j + 1);
-                            c.snr = (float)(((double)acc - w * mu) / (sg * sqrt(w)));
-                            c.reserved = 0.f; c.value = (double)acc;
-                            cands[pos] = c;
-                        }
-                    }
-                    ++p;
+    const T *src = reinterpret_cast<const T *>(out_) + (size_t)row * nout;
+    for (int i = threadIdx.x; i < len; i += kSearchThreads) {
+        const int64_t t = t0 + i;
+        x[spad(i)] = t < nout ? src[t] : (T)0;
+    }
+    __syncthreads();
+    const int base = threadIdx.x * kSearchPer;
+    const int64_t tb = t0 + base;
+    if (tb >= nout) return;
+    Acc b0 = 0;          // running B_w at the thread's first sample
+    int wprev = 0;
+    for (int p = 0; p < nw; ++p) {
+        const int w = sw[p];
+        for (int j = wprev; j < w; ++j) b0 += (Acc)x[spad(base + j)];
+        wprev = w;
+        Acc b = b0;
+        for (int i = 0; i < kSearchPer; ++i) {
+            const int64_t t = tb + i;
+            if (t + w > nout) break;
+            if (i > 0) b += (Acc)x[spad(base + i - 1 + w)] - (Acc)x[spad(base + i - 1)];
+            bool hit;
+            if constexpr (kInt) hit = b > thi[p];
+            else hit = b > thf[p];
+            if (hit) {
+                const unsigned long long pos = atomicAdd(count, 1ull);
+                if ((int64_t)pos < cap) {
+                    dd_candidate c;
+                    c.dm_idx = row; c.width_idx = sidx[p]; c.t = t;
+                    c.snr = 0.f; c.reserved = 0.f; c.value = (double)b;
+                    cands[pos] = c;
                 }
             }
         }
-    } else {
-        float *x = reinterpret_cast<float *>(sraw);
-        const float *src = reinterpret_cast<const float *>(out_) + (size_t)row * nout;
-        for (int i = threadIdx.x; i < len; i += kSearchThreads) {
-            const int64_t t = t0 + i;
-            x[i] = t < nout ? src[t] : 0.f;
-        }
-        __syncthreads();
-        for (int k = 0; k < kSearchPer; ++k) {
-            const int li = threadIdx.x + k * kSearchThreads;
-            const int64_t t = t0 + li;
-            if (t >= nout) break;
-            float acc = 0.f;
-            int p = 0;
-            for (int j = 0; j < wmax && p < nw; ++j) {
-                if (t + j >= nout) break;
-                acc += x[li + j];
-                while (p < nw && sw[p] == j + 1) {
-                    if (acc > thf[p]) {
-                        const unsigned long long pos = atomicAdd(count, 1ull);
-                        if ((int64_t)pos < cap) {
-                            dd_candidate c;
-                            c.dm_idx = row; c.width_idx = sidx[p]; c.t = t;
-                            const double w = (double)(j + 1);
-                            c.snr = (float)(((double)acc - w * mu) / (sg * sqrt(w)));
-                            c.reserved = 0.f; c.value = (double)acc;
-                            cands[pos] = c;
-                        }
-                    }
-                    ++p;
-                }
-            }
-        }
+    }
+}
+
+// S/N of the compacted hits: (B_w - w*mu) / (sigma*sqrt(w)), in double.
+__global__ void cand_snr_kernel(dd_candidate *__restrict__ cands, const unsigned long long *__restrict__ count,
+                                int64_t cap, const int32_t *__restrict__ widths, const SearchParams *__restrict__ prm)
+{
+    const int64_t n = min((int64_t)*count, cap);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double w = (double)widths[cands[i].width_idx];
+        cands[i].snr = (float)((cands[i].value - w * prm->mu) / (prm->sigma * sqrt(w)));
     }
 }
 
@@ -446,7 +368,7 @@ static size_t stat_size(const dd_plan *p)
     return p->dtype == DD_U8 ? sizeof(StatI) : sizeof(StatF);
 }
 
-static int ensure_partials(dd_plan *p, int64_t n)
+int ensure_partials_public(dd_plan *p, int64_t n)
 {
     if (n <= p->n_partials_cap) return DD_OK;
     if (p->d_partials) cudaFree(p->d_partials);
@@ -522,7 +444,7 @@ int generic_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaSt
     const int64_t ntile = (p->nsamp_out + kGenTile - 1) / kGenTile;
     if (ntile > INT32_MAX || nblk > 65535) return set_error(DD_ERR_ARG, "problem too large for kernel 1 grid");
     const int64_t np = ntile * nblk;
-    int rc = ensure_partials(p, np);
+    int rc = ensure_partials_public(p, np);
     if (rc) return rc;
     const size_t noffs = (size_t)nblk * p->nchans * kGenDms;
     const int32_t *goffs = p->d_gen;
@@ -559,7 +481,7 @@ int stats_from_out(dd_plan *p, const void *out, cudaStream_t s)
     const int64_t per = (int64_t)kStatThreads * kStatPer;
     const int64_t nb = (total + per - 1) / per;
     if (nb > INT32_MAX) return set_error(DD_ERR_ARG, "buffer too large for the stats kernel");
-    int rc = ensure_partials(p, nb);
+    int rc = ensure_partials_public(p, nb);
     if (rc) return rc;
     if (p->dtype == DD_U8)
         stats_kernel<true><<<(unsigned)nb, kStatThreads, 0, s>>>(out, total, p->d_partials);
@@ -591,7 +513,7 @@ int search_launch(dd_plan *p, const void *out, cudaStream_t s)
     for (int w : p->widths) wmax = std::max(wmax, w);
     const int64_t ntile = (p->nsamp_out + kSearchTile - 1) / kSearchTile;
     dim3 grid((unsigned)ntile, (unsigned)p->ndm);
-    const size_t smem = (size_t)(kSearchTile + wmax - 1) * 4;
+    const size_t smem = (size_t)(spad(kSearchTile + wmax - 1) + 1) * 4;
     if (isint)
         search_kernel<true><<<grid, kSearchThreads, smem, s>>>(out, p->nsamp_out, p->d_wsorted, p->nwidths,
                                                                wmax, p->d_params, p->d_cands, p->cand_cap, p->d_count);
@@ -600,6 +522,9 @@ int search_launch(dd_plan *p, const void *out, cudaStream_t s)
                                                                 wmax, p->d_params, p->d_cands, p->cand_cap, p->d_count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch search_kernel");
+    cand_snr_kernel<<<64, 256, 0, s>>>(p->d_cands, p->d_count, p->cand_cap, w_orig, p->d_params);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch cand_snr_kernel");
     return DD_OK;
 }
 

@@ -44,6 +44,7 @@ def run_case(nchans, fch1, foff, tsamp, nsamp, dm_list, widths, sigma, dtype="f3
     plan = dd.Plan(nchans, fch1, foff, tsamp, dm_list, widths, sigma, DTYPES[dtype], nsamp)
     if kernel:
         plan.set_kernel(kernel)
+    used_kernel = plan.kernel
     d_o, m_o = oracle.delays(nchans, fch1, foff, tsamp, dm_list)
     assert plan.maxshift == m_o
     assert np.array_equal(plan.delays().astype(np.int64), d_o)
@@ -77,7 +78,7 @@ def run_case(nchans, fch1, foff, tsamp, nsamp, dm_list, widths, sigma, dtype="f3
         res = compare_candidates(cands, ora, list(widths), mu_g, sg_g, mu_o, sg_o, sigma, eps)
         assert res[1] <= max_gray, f"{res[1]} gray-zone points"
     plan.close()
-    return cands, out, ora, res
+    return cands, out, ora, res, used_kernel
 
 
 SMALL = synth.workload("small_f32")
@@ -87,13 +88,14 @@ def small_pulse():
     return [synth.Pulse(dm=float(SMALL.dm_list[30]), t0=4000, width=4, amp=5.0)]
 
 
-@pytest.mark.parametrize("kernel", [0, 1])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
 @pytest.mark.parametrize("dtype", ["f32", "u8", "f16"])
 def test_small_workload_parity(dtype, kernel):
     wl = SMALL
-    cands, out, ora, res = run_case(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.nsamp, wl.dm_list,
-                                    wl.widths, wl.sigma, dtype, seed=wl.seed, pulses=small_pulse(),
-                                    kernel=kernel)
+    cands, out, ora, res, used = run_case(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.nsamp,
+                                          wl.dm_list, wl.widths, wl.sigma, dtype, seed=wl.seed,
+                                          pulses=small_pulse(), kernel=kernel)
+    assert used == (kernel or 2)
     best = cands[np.argmax(cands["snr"])]
     assert (int(best["dm_idx"]), int(best["t"]), int(best["width_idx"])) == (30, 4000, 2)
 
