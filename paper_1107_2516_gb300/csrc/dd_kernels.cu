@@ -427,7 +427,7 @@ int generic_configure(dd_plan *p)
     p->d_gen = d;
     if (chunk) {
         auto set = [&](const void *fn) {
-            return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->gen_smem);
+            return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
         };
         cudaError_t a = cudaSuccess;
         a = set((const void *)generic_kernel<float, false>);

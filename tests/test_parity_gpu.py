@@ -141,6 +141,26 @@ def test_constant_input_gives_nchans_times_value():
     plan.close()
 
 
+def test_plans_of_different_geometry_coexist():
+    # a later, smaller plan must not break launches of an earlier, larger one
+    wl = SMALL
+    arr, _ = make_input(wl.nchans, wl.nsamp, wl.fch1, wl.foff, wl.tsamp, wl.seed, small_pulse())
+    big = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, wl.sigma,
+                  dd.DD_F32, wl.nsamp)
+    small = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list[:3], [1], wl.sigma,
+                    dd.DD_F32, wl.nsamp)
+    x = to_device(arr)
+    for plan in (big, small, big):
+        out = torch.empty(plan.ndm * plan.nsamp_out, dtype=torch.float32, device="cuda")
+        plan.execute(x, wl.nsamp, out)
+        cands, total = plan.search(out)
+        if plan is big:
+            best = cands[np.argmax(cands["snr"])]
+            assert (int(best["dm_idx"]), int(best["t"])) == (30, 4000)
+    big.close()
+    small.close()
+
+
 def test_search_overflow_reports_true_count():
     wl = SMALL
     arr, _ = make_input(wl.nchans, wl.nsamp, wl.fch1, wl.foff, wl.tsamp, 5)
