@@ -472,7 +472,7 @@ int fast_configure(dd_plan *p)
     const void *fn = p->dtype == DD_F32 ? (const void *)fast_kernel<float, false>
                    : p->dtype == DD_F16 ? (const void *)fast_kernel<__half, false>
                                         : (const void *)fast_kernel<uint8_t, true>;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem(fn, p->smem_optin);
     p->fast = f;
     if (e != cudaSuccess) {
         fast_release(p);

@@ -99,6 +99,7 @@ int generic_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaSt
 int stats_from_out(dd_plan *p, const void *out, cudaStream_t s);
 int search_launch(dd_plan *p, const void *out, cudaStream_t s);
 int ensure_partials_public(dd_plan *p, int64_t n);
+cudaError_t allow_max_dynamic_smem(const void *fn, size_t optin);
 
 // dd_fast.cu
 int fast_configure(dd_plan *p);

@@ -368,6 +368,18 @@ static size_t stat_size(const dd_plan *p)
     return p->dtype == DD_U8 ? sizeof(StatI) : sizeof(StatF);
 }
 
+// The dynamic shared-memory limit is a per-kernel (not per-plan) attribute:
+// set it once to everything the device allows so that plans of different
+// geometry never lower it under one another.
+cudaError_t allow_max_dynamic_smem(const void *fn, size_t optin)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, fn);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(optin - a.sharedSizeBytes));
+}
+
 int ensure_partials_public(dd_plan *p, int64_t n)
 {
     if (n <= p->n_partials_cap) return DD_OK;
@@ -427,7 +439,7 @@ int generic_configure(dd_plan *p)
     p->d_gen = d;
     if (chunk) {
         auto set = [&](const void *fn) {
-            return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smem_optin);
+            return allow_max_dynamic_smem(fn, p->smem_optin);
         };
         cudaError_t a = cudaSuccess;
         a = set((const void *)generic_kernel<float, false>);
