@@ -146,6 +146,29 @@ DD_API int dd_plan_set_kernel(dd_plan *plan, int32_t kernel);
 /* Kernel that dd_execute will launch for this plan (1 or 2, see above). */
 DD_API int dd_plan_get_kernel(const dd_plan *plan, int32_t *kernel);
 
+/* Autotuner for the register-blocked kernel (kernel 2): runs the plan on the
+ * caller's buffers once per compiled tile configuration and raster group
+ * (see dd_plan_set_tile), times each with CUDA events on `stream`, keeps the
+ * fastest for this plan and caches the choice process-wide for plans of the
+ * same shape.  Writes out_dev (several full executions); synchronises
+ * `stream`.  A no-op (DD_OK) when kernel 2 cannot run the plan or the input
+ * rows are not 16-byte aligned. */
+DD_API int dd_plan_autotune(dd_plan *plan, const void *in_dev, int64_t in_pitch, void *out_dev,
+                            void *stream);
+
+/* Choose kernel 2's tile configuration explicitly.  config indexes the
+ * compiled list {0: 36 samples x 4 DM trials per thread, 8 warps;
+ * 1: 20 x 4, 12 warps; 2: 28 x 4, 8 warps}; raster_group (>= 1) is the
+ * number of DM blocks whose time tiles are swept together.  DD_ERR_ARG if
+ * the configuration cannot run this plan. */
+DD_API int dd_plan_set_tile(dd_plan *plan, int32_t config, int32_t raster_group);
+
+/* Current kernel-2 choice: configuration index, raster group, samples per
+ * thread and warps per block (any pointer may be NULL).  DD_ERR_ARG if
+ * kernel 2 cannot run this plan. */
+DD_API int dd_plan_get_tile(const dd_plan *plan, int32_t *config, int32_t *raster_group,
+                            int32_t *samples_per_thread, int32_t *warps_per_block);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 DD_API const char *dd_last_error(void);
 

@@ -13,7 +13,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdd.so")
-SOURCES = ["dd_api.cu", "dd_kernels.cu", "dd_fast.cu"]
+SOURCES = ["dd_api.cu", "dd_kernels.cu", "dd_fast.cu", "dd_fast_t36w8.cu", "dd_fast_t20w12.cu",
+           "dd_fast_t28w8.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -33,7 +34,7 @@ def _flags():
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(INCLUDE, "dd.h"))
     t = os.path.getmtime(obj)
     return any(os.path.getmtime(d) > t for d in deps)

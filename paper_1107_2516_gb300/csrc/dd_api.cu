@@ -228,6 +228,34 @@ int dd_plan_get_kernel(const dd_plan *plan, int32_t *kernel)
     return DD_OK;
 }
 
+int dd_plan_autotune(dd_plan *plan, const void *in_dev, int64_t in_pitch, void *out_dev, void *stream)
+{
+    if (!plan) return set_error(DD_ERR_ARG, "plan is NULL");
+    if (!in_dev || !out_dev) return set_error(DD_ERR_ARG, "NULL buffer");
+    if (in_pitch < plan->nsamp_in) return set_error(DD_ERR_ARG, "in_pitch < nsamp_in");
+    return fast_autotune(plan, in_dev, in_pitch, out_dev, (cudaStream_t)stream);
+}
+
+int dd_plan_set_tile(dd_plan *plan, int32_t config, int32_t raster_group)
+{
+    if (!plan) return set_error(DD_ERR_ARG, "plan is NULL");
+    return fast_set_tile(plan, config, raster_group);
+}
+
+int dd_plan_get_tile(const dd_plan *plan, int32_t *config, int32_t *raster_group,
+                     int32_t *samples_per_thread, int32_t *warps_per_block)
+{
+    if (!plan) return set_error(DD_ERR_ARG, "plan is NULL");
+    int c = 0, g = 0, tr = 0, nw = 0;
+    int rc = fast_get_tile(plan, &c, &g, &tr, &nw);
+    if (rc) return rc;
+    if (config) *config = c;
+    if (raster_group) *raster_group = g;
+    if (samples_per_thread) *samples_per_thread = tr;
+    if (warps_per_block) *warps_per_block = nw;
+    return DD_OK;
+}
+
 int dd_execute(dd_plan *plan, const void *in_dev, int64_t in_pitch, void *out_dev, void *stream)
 {
     if (!plan) return set_error(DD_ERR_ARG, "plan is NULL");

@@ -1,0 +1,13 @@
+// Kernel 2 instantiation: 28 samples x 4 DM trials per thread, 8 warps per block.
+#include "dd_fast_impl.cuh"
+
+namespace dd {
+
+cudaError_t fast_launch_t28w8(dd_dtype t, const FastLaunch &a, cudaStream_t s)
+{
+    return fast_launch_cfg<28, 8>(t, a, s);
+}
+
+cudaError_t fast_prepare_t28w8(size_t optin) { return fast_prepare_cfg<28, 8>(optin); }
+
+}  // namespace dd

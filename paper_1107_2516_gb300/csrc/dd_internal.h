@@ -106,5 +106,8 @@ int fast_configure(dd_plan *p);
 int fast_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStream_t s);
 void fast_release(dd_plan *p);
 int fast_error(dd_plan *p, cudaStream_t s);
+int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStream_t s);
+int fast_set_tile(dd_plan *p, int cfg, int dgroup);
+int fast_get_tile(const dd_plan *p, int *cfg, int *dgroup, int *tr, int *nw);
 
 }  // namespace dd

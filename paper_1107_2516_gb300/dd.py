@@ -27,6 +27,7 @@ assert CANDIDATE_DTYPE.itemsize == 32
 # Names of every function declared in include/dd.h.
 EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "dd_search",
            "dd_last_stats", "dd_process_host", "dd_plan_set_kernel", "dd_plan_get_kernel",
+           "dd_plan_autotune", "dd_plan_set_tile", "dd_plan_get_tile",
            "dd_last_error", "dd_version")
 
 
@@ -64,6 +65,10 @@ def load(path: Optional[str] = None):
             "dd_process_host": (C.c_int, [vp, vp, i64, vp, i64, P64, vp]),
             "dd_plan_set_kernel": (C.c_int, [vp, i32]),
             "dd_plan_get_kernel": (C.c_int, [vp, C.POINTER(i32)]),
+            "dd_plan_autotune": (C.c_int, [vp, vp, i64, vp, vp]),
+            "dd_plan_set_tile": (C.c_int, [vp, i32, i32]),
+            "dd_plan_get_tile": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                           C.POINTER(i32)]),
             "dd_last_error": (C.c_char_p, []),
             "dd_version": (C.c_char_p, []),
         }
@@ -181,6 +186,21 @@ def dd_plan_get_kernel(plan: int) -> int:
     return int(k.value)
 
 
+def dd_plan_autotune(plan: int, in_dev, in_pitch: int, out_dev, stream=None) -> None:
+    _check(load().dd_plan_autotune(plan, _ptr(in_dev), int(in_pitch), _ptr(out_dev), _stream(stream)))
+
+
+def dd_plan_set_tile(plan: int, config: int, raster_group: int) -> None:
+    _check(load().dd_plan_set_tile(plan, int(config), int(raster_group)))
+
+
+def dd_plan_get_tile(plan: int):
+    """(config, raster_group, samples_per_thread, warps_per_block) of kernel 2."""
+    v = [C.c_int32() for _ in range(4)]
+    _check(load().dd_plan_get_tile(plan, *[C.byref(x) for x in v]))
+    return tuple(int(x.value) for x in v)
+
+
 # ------------------------------------------------------------- convenience object
 
 class Plan:
@@ -214,6 +234,16 @@ class Plan:
 
     def set_kernel(self, k):
         dd_plan_set_kernel(self.handle, k)
+
+    def autotune(self, in_dev, in_pitch, out_dev, stream=None):
+        dd_plan_autotune(self.handle, in_dev, in_pitch, out_dev, stream)
+
+    def set_tile(self, config, raster_group=8):
+        dd_plan_set_tile(self.handle, config, raster_group)
+
+    @property
+    def tile(self):
+        return dd_plan_get_tile(self.handle)
 
     @property
     def kernel(self):

@@ -38,12 +38,14 @@ def to_device(arr: np.ndarray):
 
 
 def run_case(nchans, fch1, foff, tsamp, nsamp, dm_list, widths, sigma, dtype="f32", seed=0,
-             pulses=(), pitch=None, kernel=0, check_cands=True, max_gray=0):
+             pulses=(), pitch=None, kernel=0, check_cands=True, max_gray=0, tile=None):
     arr, _ = make_input(nchans, nsamp, fch1, foff, tsamp, seed, pulses, dtype, pitch)
     pitch = arr.shape[1]
     plan = dd.Plan(nchans, fch1, foff, tsamp, dm_list, widths, sigma, DTYPES[dtype], nsamp)
     if kernel:
         plan.set_kernel(kernel)
+    if tile is not None:
+        plan.set_tile(*tile)
     used_kernel = plan.kernel
     d_o, m_o = oracle.delays(nchans, fch1, foff, tsamp, dm_list)
     assert plan.maxshift == m_o
@@ -98,6 +100,42 @@ def test_small_workload_parity(dtype, kernel):
     assert used == (kernel or 2)
     best = cands[np.argmax(cands["snr"])]
     assert (int(best["dm_idx"]), int(best["t"]), int(best["width_idx"])) == (30, 4000, 2)
+
+
+@pytest.mark.parametrize("tile", [(0, 1), (0, 3), (1, 8), (1, 2), (2, 16)])
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_small_workload_tile_configs(dtype, tile):
+    # every compiled tile configuration and several raster groups (incl. a
+    # ragged last group) give the oracle's result
+    wl = SMALL
+    cands, out, ora, res, used = run_case(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.nsamp,
+                                          wl.dm_list, wl.widths, wl.sigma, dtype, seed=wl.seed,
+                                          pulses=small_pulse(), kernel=2, tile=tile)
+    assert used == 2
+
+
+def test_autotune_keeps_parity():
+    wl = SMALL
+    arr, _ = make_input(wl.nchans, wl.nsamp, wl.fch1, wl.foff, wl.tsamp, wl.seed, small_pulse())
+    plan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, wl.sigma,
+                   dd.DD_F32, wl.nsamp)
+    x = to_device(arr)
+    out = torch.empty(wl.ndm * plan.nsamp_out, dtype=torch.float32, device="cuda")
+    plan.autotune(x, wl.nsamp, out)
+    cfg, group, tr, nw = plan.tile
+    assert 0 <= cfg < 3 and group in (4, 8, 16) and tr in (20, 28, 36) and nw in (8, 12)
+    plan.execute(x, wl.nsamp, out)
+    torch.cuda.synchronize()
+    d_o, m_o = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
+    ora = oracle.dedisperse(arr, d_o, plan.nsamp_out)
+    err = np.max(np.abs(out.cpu().numpy().reshape(wl.ndm, -1) - ora))
+    assert err <= fp_tol(wl.nchans)
+    # a second plan of the same shape starts from the cached choice
+    plan2 = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, wl.sigma,
+                    dd.DD_F32, wl.nsamp)
+    assert plan2.tile[:2] == (cfg, group)
+    plan.close()
+    plan2.close()
 
 
 EDGE = [
