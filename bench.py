@@ -103,30 +103,50 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _oracle_sample(ndm_s, nt_s):
+    """Inputs for one bounded oracle sample of the LOFAR-like workload: ndm_s DM
+    rows spread evenly over the 2000 trials, nt_s output samples."""
+    import oracle
+    wl = synth.workload(WORKLOAD)
+    oracle.build()
+    d_all, m = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
+    rows = np.linspace(0, wl.ndm - 1, ndm_s).astype(np.int64)
+    d = np.ascontiguousarray(d_all[rows])
+    x = synth.noise_f32(wl.nchans, nt_s + m, seed=wl.seed)
+    return wl, x, d
+
+
+def _oracle_step(wl, x, d, nt_s):
+    """One oracle pass over the sample: de-dispersion, statistics, search."""
+    import oracle
+    t0 = time.perf_counter()
+    out = oracle.dedisperse(x, d, nt_s)
+    mu, sg = oracle.stats(out)
+    oracle.search(out, list(wl.widths), mu, sg, wl.sigma)
+    return time.perf_counter() - t0
+
+
+REF_SAMPLE = (64, 131072)        # per --impl reference step (about 1 s on 16 cores)
+BASELINE_SAMPLE = (256, 262144)  # the GPU line's cpu_baseline (about 10-30 s)
+
+
 def run_reference(args, rank, world):
     """CPU oracle on a bounded sample of the same workload (rank 0 only)."""
     import oracle
     if rank != 0:
         return
-    wl = synth.workload(WORKLOAD)
-    oracle.build()
-    d_all, m = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
-    ndm_s, nt_s = 32, 16384         # 32 DM rows spread over the range x 16384 samples
-    rows = np.linspace(0, wl.ndm - 1, ndm_s).astype(np.int64)
-    d = np.ascontiguousarray(d_all[rows])
-    x = synth.noise_f32(wl.nchans, nt_s + m, seed=wl.seed)
+    ndm_s, nt_s = REF_SAMPLE
+    wl, x, d = _oracle_sample(ndm_s, nt_s)
     cores = oracle.num_threads()
     times = []
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        out = oracle.dedisperse(x, d, nt_s)
-        mu, sg = oracle.stats(out)
-        oracle.search(out, list(wl.widths), mu, sg, wl.sigma)
-        dt = time.perf_counter() - t0
+        dt = _oracle_step(wl, x, d, nt_s)
         if i >= args.warmup:
             times.append(dt)
     tm = statistics.median(times)
     value = ndm_s * nt_s / tm
+    sample = (f"{ndm_s} of 2000 DM rows x {nt_s} of 1028179 samples per step: "
+              "dedisperse + stats + search")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -134,10 +154,9 @@ def run_reference(args, rank, world):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "lofar_f32: 1024 ch, 150 MHz top, foff -0.01171875 MHz, "
                    "tsamp 163.84 us, 2^20 samples, 2000 DMs 0-99.95 step 0.05",
-                   "sample": f"{ndm_s} DM rows x {nt_s} samples per step"},
+                   "sample": sample},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": cores, "kind": "oracle",
-                         "sample": f"{ndm_s} of 2000 DM rows x {nt_s} of 1028179 samples, "
-                                   "dedisperse + stats + search"},
+                         "sample": sample},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -146,21 +165,13 @@ def run_reference(args, rank, world):
 def cpu_baseline_sample():
     """Oracle on a bounded sample (about 10-30 s of CPU work), for the GPU line."""
     import oracle
-    wl = synth.workload(WORKLOAD)
-    oracle.build()
-    d_all, m = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
-    ndm_s, nt_s = 32, 16384
-    rows = np.linspace(0, wl.ndm - 1, ndm_s).astype(np.int64)
-    d = np.ascontiguousarray(d_all[rows])
-    x = synth.noise_f32(wl.nchans, nt_s + m, seed=wl.seed)
-    t0 = time.perf_counter()
-    out = oracle.dedisperse(x, d, nt_s)
-    mu, sg = oracle.stats(out)
-    oracle.search(out, list(wl.widths), mu, sg, wl.sigma)
-    dt = time.perf_counter() - t0
+    ndm_s, nt_s = BASELINE_SAMPLE
+    wl, x, d = _oracle_sample(ndm_s, nt_s)
+    dt = _oracle_step(wl, x, d, nt_s)
     return {"value": ndm_s * nt_s / dt, "unit": METRIC, "cores": oracle.num_threads(),
             "kind": "oracle", "seconds": dt,
-            "sample": f"{ndm_s} of 2000 DM rows x {nt_s} samples: dedisperse + stats + search"}
+            "sample": f"{ndm_s} of 2000 DM rows x {nt_s} of 1028179 samples: "
+                      "dedisperse + stats + search, FP64, all host cores"}
 
 
 def run_ours(args, rank, world, local_rank):
