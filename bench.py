@@ -34,6 +34,9 @@ import synth  # noqa: E402
 
 METRIC = "DM-trial·samples/s"
 WORKLOAD = "lofar_f32"
+# ncu DRAM bytes (read + write) per de-dispersion launch, keyed by the kernel-2
+# (tile configuration, raster group) the capture used
+PROFILED_TRAFFIC = {(1, 16): 21.01e9}
 
 
 def _pulses(wl, nout, seed):
@@ -275,7 +278,11 @@ def run_ours(args, rank, world, local_rank):
     roof = {"bound": "alu", "kernel": f"dd kernel {kernel_id} (de-dispersion{tile_s})",
             "achieved": achieved, "peak": peak, "unit": "Gadd/s", "frac": achieved / peak,
             "peak_basis": f"{sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",
-            "traffic": None,
+            # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
+            # capture summarised in profiles/dedisp_kernel2_lofar_f32.md; only for
+            # the tile it was taken with (null otherwise)
+            "traffic": PROFILED_TRAFFIC.get(tuple(tile[:2])) if tile else None,
+            "traffic_unit": "bytes per launch",
             "kernel_ms": ker_ms}
     if clk.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (sm * 128 * clk["sm_mhz"] * 1e6 / 1e9)

@@ -59,7 +59,7 @@ def main(argv=None):
     units = len(dms) * plan.nsamp_out
     tile = plan.tile if plan.kernel == 2 else None
     print(f"kernel {plan.kernel} tile {tile} dms {a.dm_lo}+{len(dms)} nsamp {a.nsamp}: {ms:.2f} ms, "
-          f"{units / ms / 1e6:.3e} DM-trial.samples/s, {units * wl.nchans / ms / 1e9:.2f} Tadd/s")
+          f"{units / (ms / 1e3):.3e} DM-trial.samples/s, {units * wl.nchans / ms / 1e9:.2f} Tadd/s")
     plan.close()
 
 
