@@ -169,6 +169,23 @@ DD_API int dd_plan_set_tile(dd_plan *plan, int32_t config, int32_t raster_group)
 DD_API int dd_plan_get_tile(const dd_plan *plan, int32_t *config, int32_t *raster_group,
                             int32_t *samples_per_thread, int32_t *warps_per_block);
 
+/* Allocation-free statistics (no counterpart in the paper).  For callers that
+ * cannot call cudaMalloc — e.g. a real-time pipeline whose device memory is
+ * budgeted once at start-up, where an allocation could synchronise the device
+ * and stall live streams, or code running where another runtime owns the
+ * allocator.  Writes mu = mean and sigma = population standard deviation of
+ * the n float32 values at x_dev (device) to mu_sigma_dev[0] and [1] (device,
+ * caller-owned), asynchronously on `stream`.  Needs no plan and allocates
+ * nothing: its per-block partials live in a fixed 1.5 MB device array that
+ * every GPU loading the library holds until exit, which limits n to
+ * 1 <= n <= 268435456 (2^28); larger n returns DD_ERR_ARG without launching.
+ * The first call on each device looks up that array's device address (with
+ * the device current); make that first call before any stream capture.
+ * Every call on a device shares the array, so calls whose kernels overlap on
+ * the GPU (different streams, no ordering between them) race and may return
+ * wrong values; calls ordered on one stream are safe. */
+DD_API int dd_stats_f32_noalloc(const float *x_dev, int64_t n, double *mu_sigma_dev, void *stream);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 DD_API const char *dd_last_error(void);
 

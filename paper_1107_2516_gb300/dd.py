@@ -28,7 +28,7 @@ assert CANDIDATE_DTYPE.itemsize == 32
 EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "dd_search",
            "dd_last_stats", "dd_process_host", "dd_plan_set_kernel", "dd_plan_get_kernel",
            "dd_plan_autotune", "dd_plan_set_tile", "dd_plan_get_tile",
-           "dd_last_error", "dd_version")
+           "dd_stats_f32_noalloc", "dd_last_error", "dd_version")
 
 
 class DDError(RuntimeError):
@@ -67,6 +67,7 @@ def load(path: Optional[str] = None):
             "dd_plan_get_kernel": (C.c_int, [vp, C.POINTER(i32)]),
             "dd_plan_autotune": (C.c_int, [vp, vp, i64, vp, vp]),
             "dd_plan_set_tile": (C.c_int, [vp, i32, i32]),
+            "dd_stats_f32_noalloc": (C.c_int, [vp, i64, vp, vp]),
             "dd_plan_get_tile": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                            C.POINTER(i32)]),
             "dd_last_error": (C.c_char_p, []),
@@ -199,6 +200,13 @@ def dd_plan_get_tile(plan: int):
     v = [C.c_int32() for _ in range(4)]
     _check(load().dd_plan_get_tile(plan, *[C.byref(x) for x in v]))
     return tuple(int(x.value) for x in v)
+
+
+def dd_stats_f32_noalloc(x_dev, n: int, mu_sigma_dev, stream=None) -> None:
+    """Mean and standard deviation of n float32 device values into mu_sigma_dev[0:2]
+    (device, float64) without any allocation; for callers that cannot allocate
+    device memory after start-up.  At most 2**28 values; see include/dd.h."""
+    _check(load().dd_stats_f32_noalloc(_ptr(x_dev), int(n), _ptr(mu_sigma_dev), _stream(stream)))
 
 
 # ------------------------------------------------------------- convenience object
