@@ -58,6 +58,7 @@ extern "C" {
 #endif
 
 typedef struct dd_plan dd_plan;
+typedef struct dd_batch dd_batch;
 
 typedef enum { DD_F32 = 0, DD_U8 = 1, DD_F16 = 2 } dd_dtype;
 
@@ -168,6 +169,53 @@ DD_API int dd_plan_set_tile(dd_plan *plan, int32_t config, int32_t raster_group)
  * kernel 2 cannot run this plan. */
 DD_API int dd_plan_get_tile(const dd_plan *plan, int32_t *config, int32_t *raster_group,
                             int32_t *samples_per_thread, int32_t *warps_per_block);
+
+/* ---------------------------------------------------------------------
+ * Batched beams.  The paper's kernel processes one buffer at a time
+ * (Section 3.1); a batch runs the Section 3.1 sum for several plans (beams of
+ * different channel counts, lengths, DM grids and input types) in ONE
+ * persistent launch that pulls (beam, DM block, time tile) work items from a
+ * device queue ordered heaviest first, followed by each beam's Section 3
+ * search.  Each beam's output and candidates are those its plan alone would
+ * produce (the same arithmetic in the same order).
+ * ------------------------------------------------------------------- */
+
+/* Group `nplans` plans (not owned; they must outlive the batch and live on
+ * the current device).  Beams whose plan cannot use the register-blocked
+ * kernel are still accepted and run by their own launch inside the batch. */
+DD_API int dd_batch_create(dd_plan *const *plans, int32_t nplans, dd_batch **batch_out);
+
+/* Free the batch (its graph, queue and descriptors; not the plans). */
+DD_API int dd_batch_destroy(dd_batch *batch);
+
+/* Asynchronous: de-disperse every beam (in_devs[i], in_pitches[i] ->
+ * out_devs[i], layouts as dd_execute) and run every beam's search kernels on
+ * `stream`.  Results are read with dd_batch_results. */
+DD_API int dd_batch_execute(dd_batch *batch, const void *const *in_devs, const int64_t *in_pitches,
+                            void *const *out_devs, void *stream);
+
+/* Record dd_batch_execute's work for these buffers as a CUDA graph (stream
+ * capture on `stream`); dd_batch_launch then replays it.  Allocates what the
+ * launches need before capturing. */
+DD_API int dd_batch_capture(dd_batch *batch, const void *const *in_devs, const int64_t *in_pitches,
+                            void *const *out_devs, void *stream);
+
+/* Replay the captured graph on `stream` (asynchronous). */
+DD_API int dd_batch_launch(dd_batch *batch, void *stream);
+
+/* Synchronise `stream` and return beam `beam`'s candidates of the last
+ * execute/launch, as dd_search does. */
+DD_API int dd_batch_results(dd_batch *batch, int32_t beam, dd_candidate *cand_host, int64_t capacity,
+                            int64_t *n_found, void *stream);
+
+/* Time the persistent launch with each compiled tile configuration that all
+ * batched beams can use, keep the fastest (writes out_devs; synchronises). */
+DD_API int dd_batch_autotune(dd_batch *batch, const void *const *in_devs, const int64_t *in_pitches,
+                             void *const *out_devs, void *stream);
+
+/* Tile configuration the persistent launch uses (-1 if no beam uses it),
+ * number of work items, and number of beams run by their own launch. */
+DD_API int dd_batch_info(const dd_batch *batch, int32_t *config, int64_t *nitems, int32_t *n_separate);
 
 /* Allocation-free statistics (no counterpart in the paper).  For callers that
  * cannot call cudaMalloc — e.g. a real-time pipeline whose device memory is

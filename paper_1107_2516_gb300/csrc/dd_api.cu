@@ -77,6 +77,41 @@ static int ensure_cands(dd_plan *p, int64_t cap)
     return DD_OK;
 }
 
+// Synchronise `s`, read the search results of the plan's last search_launch
+// (dev_cap = the candidate capacity that launch used) and sort them.
+int search_readback(dd_plan *plan, dd_candidate *cand_host, int64_t capacity, int64_t *n_found,
+                    cudaStream_t s, int64_t dev_cap)
+{
+    cudaError_t e = cudaMemcpyAsync(plan->h_count, plan->d_count, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(plan->h_params, plan->d_params, sizeof(SearchParams), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "search readback");
+    int rc = fast_error(plan, s);
+    if (rc) return rc;
+    const int64_t total = (int64_t)*plan->h_count;
+    const int64_t n = std::min<int64_t>(std::min<int64_t>(total, dev_cap), capacity);
+    plan->last_mu = plan->h_params->mu;
+    plan->last_sigma = plan->h_params->sigma;
+    if (n > 0) {
+        e = cudaMemcpyAsync(cand_host, plan->d_cands, (size_t)n * sizeof(dd_candidate),
+                            cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "candidate readback");
+        std::sort(cand_host, cand_host + n, [](const dd_candidate &a, const dd_candidate &b) {
+            if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
+            if (a.t != b.t) return a.t < b.t;
+            return a.width_idx < b.width_idx;
+        });
+    }
+    *n_found = total;
+    if (total > capacity || total > dev_cap)
+        return set_error(DD_ERR_OVERFLOW, "%lld candidates exceed capacity %lld",
+                         (long long)total, (long long)std::min(capacity, dev_cap));
+    return DD_OK;
+}
+
 }  // namespace dd
 
 using namespace dd;
@@ -282,36 +317,10 @@ int dd_search(dd_plan *plan, const void *out_dev, dd_candidate *cand_host, int64
     const int64_t saved_cap = plan->cand_cap;
     plan->cand_cap = std::max<int64_t>(capacity, 0);
     rc = search_launch(plan, out_dev, s);
+    const int64_t dev_cap = plan->cand_cap;
     plan->cand_cap = saved_cap;
     if (rc) return rc;
-    cudaError_t e = cudaMemcpyAsync(plan->h_count, plan->d_count, sizeof(unsigned long long),
-                                    cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(plan->h_params, plan->d_params, sizeof(SearchParams), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "search readback");
-    rc = fast_error(plan, s);
-    if (rc) return rc;
-    const int64_t total = (int64_t)*plan->h_count;
-    const int64_t n = std::min<int64_t>(total, capacity);
-    plan->last_mu = plan->h_params->mu;
-    plan->last_sigma = plan->h_params->sigma;
-    if (n > 0) {
-        e = cudaMemcpyAsync(cand_host, plan->d_cands, (size_t)n * sizeof(dd_candidate),
-                            cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) return cuda_fail(e, "candidate readback");
-        std::sort(cand_host, cand_host + n, [](const dd_candidate &a, const dd_candidate &b) {
-            if (a.dm_idx != b.dm_idx) return a.dm_idx < b.dm_idx;
-            if (a.t != b.t) return a.t < b.t;
-            return a.width_idx < b.width_idx;
-        });
-    }
-    *n_found = total;
-    if (total > capacity)
-        return set_error(DD_ERR_OVERFLOW, "%lld candidates exceed capacity %lld",
-                         (long long)total, (long long)capacity);
-    return DD_OK;
+    return search_readback(plan, cand_host, capacity, n_found, s, dev_cap);
 }
 
 int dd_last_stats(const dd_plan *plan, double *mu, double *sigma)

@@ -306,3 +306,298 @@ void fast_release(dd_plan *p)
 }
 
 }  // namespace dd
+
+// ===================================================================== batch
+// Several plans (beams) in one persistent launch of batch_kernel.
+
+struct dd_batch {
+    std::vector<dd_plan *> plans;
+    int device = 0;
+    int cfg = -1;                          // shared tile configuration (-1: no persistent launch)
+    std::vector<int> k2;                   // beams in the persistent launch
+    std::vector<int> sep;                  // beams run by their own dd_execute launch
+    uint2 *d_items = nullptr;
+    int nitems = 0;
+    dd::FastLaunch *d_beams = nullptr, *h_beams = nullptr;   // h_beams pinned (graph-capturable copy)
+    unsigned int *d_counter = nullptr;
+    int *d_err = nullptr;
+    int bar_off = 0;
+    size_t smem = 0;
+    int grid = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace dd {
+
+static FastPlan *fp(const dd_plan *p) { return static_cast<FastPlan *>(p->fast); }
+
+// Work items for configuration k: every (beam, linear tile) of the beams that
+// can use it, heaviest beams (most channels per item) first.
+static int batch_build(dd_batch *B, int k)
+{
+    B->k2.clear();
+    B->sep.clear();
+    for (int i = 0; i < (int)B->plans.size(); ++i) {
+        const FastPlan *f = fp(B->plans[i]);
+        if (k >= 0 && f && f->cfg[k].ok) B->k2.push_back(i); else B->sep.push_back(i);
+    }
+    std::vector<int> order = B->k2;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return B->plans[a]->nchans > B->plans[b]->nchans;
+    });
+    std::vector<uint2> items;
+    int bar_off = 0;
+    for (int i : order) {
+        const dd_plan *p = B->plans[i];
+        const FastCfgData &c = fp(p)->cfg[k];
+        const int64_t ntile = (p->nsamp_out + 32 * c.tr - 1) / (32 * c.tr);
+        const int64_t n = ntile * c.nblk;
+        if ((int64_t)items.size() + n > INT32_MAX) return set_error(DD_ERR_ARG, "batch too large");
+        for (int64_t l = 0; l < n; ++l) items.push_back(make_uint2((unsigned)i, (unsigned)l));
+        bar_off = std::max(bar_off, c.bar_off);
+    }
+    if (B->d_items) cudaFree(B->d_items);
+    B->d_items = nullptr;
+    B->nitems = (int)items.size();
+    B->cfg = B->k2.empty() ? -1 : k;
+    B->bar_off = bar_off;
+    B->smem = (size_t)bar_off + kStages * sizeof(uint64_t);
+    if (!items.empty()) {
+        cudaError_t e = cudaMalloc(&B->d_items, items.size() * sizeof(uint2));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B->d_items, items.data(), items.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "batch work items");
+    }
+    return DD_OK;
+}
+
+// Everything the launches need, allocated before any capture.
+static int batch_prepare(dd_batch *B)
+{
+    for (int i : B->k2) {
+        dd_plan *p = B->plans[i];
+        const FastCfgData &c = fp(p)->cfg[B->cfg];
+        const int64_t ntile = (p->nsamp_out + 32 * c.tr - 1) / (32 * c.tr);
+        int rc = ensure_partials_public(p, ntile * c.nblk);
+        if (rc) return rc;
+    }
+    return DD_OK;
+}
+
+static int batch_enqueue(dd_batch *B, const void *const *ins, const int64_t *pitches, void *const *outs,
+                         cudaStream_t s)
+{
+    for (size_t i = 0; i < B->plans.size(); ++i) {
+        if (!ins[i] || !outs[i]) return set_error(DD_ERR_ARG, "NULL buffer for beam %d", (int)i);
+        if (pitches[i] < B->plans[i]->nsamp_in) return set_error(DD_ERR_ARG, "pitch < nsamp_in for beam %d", (int)i);
+    }
+    int rc = batch_prepare(B);
+    if (rc) return rc;
+    std::vector<int> own(B->sep);
+    if (B->cfg >= 0) {
+        for (int i : B->k2) {
+            dd_plan *p = B->plans[i];
+            FastPlan *f = fp(p);
+            if (((uintptr_t)ins[i] & 15u) || (pitches[i] % f->al))
+                return set_error(DD_ERR_ARG, "beam %d: input rows must be 16-byte aligned in a batch", i);
+            const FastCfgData &c = f->cfg[B->cfg];
+            FastLaunch &a = B->h_beams[i];
+            a.in = ins[i]; a.pitch = pitches[i];
+            a.nsamp_in_al = (p->nsamp_in + f->al - 1) / f->al * f->al;
+            a.nchans = p->nchans; a.ndm = p->ndm; a.nout = p->nsamp_out;
+            a.desc = c.d_desc; a.base = c.d_base; a.goff = c.d_goff;
+            a.rs = c.rs; a.ch = c.ch; a.bar_off = B->bar_off; a.nblk = c.nblk;
+            a.ntile = (p->nsamp_out + 32 * c.tr - 1) / (32 * c.tr);
+            a.dgroup = std::max(1, std::min(f->dgroup, c.nblk));
+            a.out = outs[i]; a.partials = p->d_partials; a.err = f->d_err; a.smem = B->smem;
+            a.dtype = (int)p->dtype;
+        }
+        cudaError_t e = cudaMemcpyAsync(B->d_beams, B->h_beams, B->plans.size() * sizeof(FastLaunch),
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return cuda_fail(e, "batch setup");
+        BatchLaunch bl;
+        bl.beams = B->d_beams; bl.items = B->d_items; bl.nitems = B->nitems;
+        bl.bar_off = B->bar_off; bl.counter = B->d_counter; bl.err = B->d_err;
+        switch (B->cfg) {
+        case 0: e = batch_launch_t36w8(bl, B->grid, B->smem, s); break;
+        case 1: e = batch_launch_t20w12(bl, B->grid, B->smem, s); break;
+        default: e = batch_launch_t28w8(bl, B->grid, B->smem, s); break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "launch batch_kernel");
+        for (int i : B->k2) {
+            dd_plan *p = B->plans[i];
+            p->n_partials = B->h_beams[i].ntile * B->h_beams[i].nblk;
+            p->stats_out = outs[i];
+        }
+    }
+    for (int i : own) {
+        rc = generic_execute(B->plans[i], ins[i], pitches[i], outs[i], s);
+        if (rc) return rc;
+    }
+    for (size_t i = 0; i < B->plans.size(); ++i) {
+        rc = search_launch(B->plans[i], outs[i], s);
+        if (rc) return rc;
+    }
+    return DD_OK;
+}
+
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" {
+
+int dd_batch_create(dd_plan *const *plans, int32_t nplans, dd_batch **out)
+{
+    if (!out) return set_error(DD_ERR_ARG, "batch_out is NULL");
+    *out = nullptr;
+    if (!plans || nplans < 1) return set_error(DD_ERR_ARG, "need >= 1 plan");
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int i = 0; i < nplans; ++i) {
+        if (!plans[i]) return set_error(DD_ERR_ARG, "plan %d is NULL", i);
+        if (plans[i]->device != dev) return set_error(DD_ERR_ARG, "plan %d lives on another device", i);
+    }
+    dd_batch *B = new dd_batch();
+    B->plans.assign(plans, plans + nplans);
+    B->device = dev;
+    B->grid = std::max(1, plans[0]->sm_count);
+    // first configuration every kernel-2 beam can use
+    int k = -1;
+    for (int c = 0; c < kNumFastCfg && k < 0; ++c) {
+        bool all = false, some = false;
+        for (int i = 0; i < nplans; ++i) {
+            const FastPlan *f = fp(plans[i]);
+            if (!f) continue;
+            some = true;
+            all = f->cfg[c].ok;
+            if (!all) break;
+        }
+        if (some && all) k = c;
+    }
+    cudaError_t e = cudaMalloc(&B->d_beams, nplans * sizeof(FastLaunch));
+    if (e == cudaSuccess) e = cudaMallocHost(&B->h_beams, nplans * sizeof(FastLaunch));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_counter, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(B->d_err, 0, sizeof(int));
+    int rc = e == cudaSuccess ? DD_OK : cuda_fail(e, "batch allocation");
+    if (rc == DD_OK) {
+        memset(B->h_beams, 0, nplans * sizeof(FastLaunch));
+        rc = batch_build(B, k);
+    }
+    if (rc != DD_OK) { dd_batch_destroy(B); return rc; }
+    *out = B;
+    return DD_OK;
+}
+
+int dd_batch_destroy(dd_batch *B)
+{
+    if (!B) return DD_OK;
+    cudaDeviceSynchronize();
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->d_items) cudaFree(B->d_items);
+    if (B->d_beams) cudaFree(B->d_beams);
+    if (B->h_beams) cudaFreeHost(B->h_beams);
+    if (B->d_counter) cudaFree(B->d_counter);
+    if (B->d_err) cudaFree(B->d_err);
+    delete B;
+    return DD_OK;
+}
+
+int dd_batch_execute(dd_batch *B, const void *const *ins, const int64_t *pitches, void *const *outs, void *stream)
+{
+    if (!B || !ins || !pitches || !outs) return set_error(DD_ERR_ARG, "NULL argument");
+    return batch_enqueue(B, ins, pitches, outs, (cudaStream_t)stream);
+}
+
+int dd_batch_capture(dd_batch *B, const void *const *ins, const int64_t *pitches, void *const *outs, void *stream)
+{
+    if (!B || !ins || !pitches || !outs) return set_error(DD_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!s) return set_error(DD_ERR_ARG, "graph capture needs a non-default stream");
+    int rc = batch_prepare(B);
+    if (rc) return rc;
+    if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+    if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    rc = batch_enqueue(B, ins, pitches, outs, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    B->graph = g;
+    e = cudaGraphInstantiate(&B->exec, g, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return DD_OK;
+}
+
+int dd_batch_launch(dd_batch *B, void *stream)
+{
+    if (!B || !B->exec) return set_error(DD_ERR_ARG, "no captured graph");
+    cudaError_t e = cudaGraphLaunch(B->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+    return DD_OK;
+}
+
+int dd_batch_results(dd_batch *B, int32_t beam, dd_candidate *cand_host, int64_t capacity, int64_t *n_found,
+                     void *stream)
+{
+    if (!B || beam < 0 || beam >= (int)B->plans.size()) return set_error(DD_ERR_ARG, "bad beam index");
+    if (!n_found || capacity < 0 || (capacity > 0 && !cand_host)) return set_error(DD_ERR_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, B->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "batch status");
+    if (h) return set_error(h, "batch kernel gave up waiting for its input copies");
+    dd_plan *p = B->plans[beam];
+    return search_readback(p, cand_host, capacity, n_found, s, p->cand_cap);
+}
+
+int dd_batch_autotune(dd_batch *B, const void *const *ins, const int64_t *pitches, void *const *outs, void *stream)
+{
+    if (!B) return set_error(DD_ERR_ARG, "batch is NULL");
+    if (B->cfg < 0) return DD_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return set_error(DD_ERR_CUDA, "cudaEventCreate");
+    float best = 1e30f;
+    int bk = B->cfg, rc = DD_OK;
+    for (int k = 0; k < kNumFastCfg && rc == DD_OK; ++k) {
+        bool all = true;
+        for (int i = 0; i < (int)B->plans.size(); ++i) {
+            const FastPlan *f = fp(B->plans[i]);
+            if (f && !f->cfg[k].ok) all = false;
+        }
+        if (!all) continue;
+        rc = batch_build(B, k);
+        if (!rc) rc = batch_enqueue(B, ins, pitches, outs, s);           // warm-up
+        if (!rc) { cudaEventRecord(e0, s); rc = batch_enqueue(B, ins, pitches, outs, s); cudaEventRecord(e1, s); }
+        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(DD_ERR_CUDA, "autotune sync");
+        float ms = 0.f;
+        if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+        if (!rc && ms < best) { best = ms; bk = k; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+    if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+    return batch_build(B, bk);
+}
+
+int dd_batch_info(const dd_batch *B, int32_t *config, int64_t *nitems, int32_t *n_separate)
+{
+    if (!B) return set_error(DD_ERR_ARG, "batch is NULL");
+    if (config) *config = B->cfg;
+    if (nitems) *nitems = B->nitems;
+    if (n_separate) *n_separate = (int32_t)B->sep.size();
+    return DD_OK;
+}
+
+}  // extern "C"

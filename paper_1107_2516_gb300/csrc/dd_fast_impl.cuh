@@ -46,6 +46,7 @@ struct FastLaunch {
     void *out, *partials;
     int *err;
     size_t smem;
+    int dtype;                   // dd_dtype of `in` (batched launches)
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -239,45 +240,33 @@ __device__ __forceinline__ void chan_dispatch(float (&acc)[kDR][TR], const Tin *
 }
 
 // ------------------------------------------------------------------- kernel
+// One work item: DM block `blk` (4*NW trials) x the time tile starting at t0
+// of the plan described by `a`.  `gstage` is the block's running stage count:
+// the mbarrier ring persists across the items a persistent block processes,
+// so stage s of this item uses buffer (gstage+s) % kStages and the parity of
+// (gstage+s) / kStages.  Returns false if a bounded wait gave up.
 template <typename Tin, bool kInt, int TR, int NW>
-__global__ void __launch_bounds__(NW * 32, 1) fast_kernel(FastLaunch a)
+__device__ __forceinline__ bool process_tile(const FastLaunch &a, int blk, int64_t t0, int64_t lin,
+                                             unsigned char *smem, uint64_t *bar, uint32_t &gstage)
 {
     static_assert(TR % 8 == 4, "TR must be 4 x odd: conflict-free 16-byte window loads");
     constexpr int kTile = 32 * TR, kDmBlk = kDR * NW;
-    extern __shared__ __align__(128) unsigned char smem[];
     const Tin *__restrict__ in = static_cast<const Tin *>(a.in);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nchans = a.nchans, rs = a.rs, ch = a.ch;
-
-    // Raster: DM blocks in groups of a.dgroup; within a group the time tiles
-    // advance slowest, so concurrently resident blocks read nearby input
-    // spans (better L2 reuse than sweeping all DM blocks of a tile at once).
-    const int64_t lin = blockIdx.x;
-    const int64_t per_group = (int64_t)a.dgroup * a.ntile;
-    const int64_t grp = lin / per_group;
-    const int64_t rr = lin - grp * per_group;
-    const int gsize = min(a.dgroup, a.nblk - (int)grp * a.dgroup);
-    const int blk = (int)grp * a.dgroup + (int)(rr % gsize);
-    const int64_t t0 = (rr / gsize) * kTile;
     const int dm0 = blk * kDmBlk;
 
-    // layout: [kStages][ch][rs] Tin rows | [kStages][ch][NW] desc | ... | mbar at bar_off
-    // (the epilogue reuses [0, bar_off) for the output transpose)
+    // layout: [kStages][ch][rs] Tin rows | [kStages][ch][NW] desc | ... | mbar
+    // (the epilogue reuses the start of shared memory for the output transpose)
     const size_t stage_elems = (size_t)ch * rs;
     Tin *rows = reinterpret_cast<Tin *>(smem);
     uint32_t *sdesc = reinterpret_cast<uint32_t *>(smem + kStages * stage_elems * sizeof(Tin));
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.bar_off);
 
     const uint32_t *bdesc = a.desc + (size_t)blk * nchans * NW;
     const int32_t *bbase = a.base + (size_t)blk * nchans;
     const int32_t *bgoff = a.goff + (size_t)blk * nchans * NW * kDR;
     const int nst = (nchans + ch - 1) / ch;
-
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
+    const uint32_t g0 = gstage;
 
     // bytes of one row copy: clamped at the (aligned) end of the input row
     auto row_bytes = [&](int c, int64_t &g) -> uint32_t {
@@ -287,7 +276,7 @@ __global__ void __launch_bounds__(NW * 32, 1) fast_kernel(FastLaunch a)
         return (uint32_t)(n * (int64_t)sizeof(Tin));
     };
     auto issue = [&](int s) {
-        const int buf = s % kStages;
+        const int buf = (int)((g0 + s) % kStages);
         const int c0 = s * ch;
         const int cn = min(ch, nchans - c0);
         uint32_t bytes = (uint32_t)(cn * NW * sizeof(uint32_t));
@@ -315,11 +304,12 @@ __global__ void __launch_bounds__(NW * 32, 1) fast_kernel(FastLaunch a)
 
     bool ok = true;
     for (int s = 0; s < nst; ++s) {
-        // buffer (s+kStages-1)%kStages was last read in stage s-1, which every
+        // buffer of stage s+kStages-1 was last read in stage s-1, which every
         // thread finished before the __syncthreads that ended it
         if (tid == 0 && s + kStages - 1 < nst) issue(s + kStages - 1);
-        const int buf = s % kStages;
-        if (!mbar_wait(&bar[buf], (uint32_t)((s / kStages) & 1), a.err)) { ok = false; break; }
+        const uint32_t g = g0 + s;
+        const int buf = (int)(g % kStages);
+        if (!mbar_wait(&bar[buf], (g / kStages) & 1u, a.err)) { ok = false; break; }
         const int c0 = s * ch;
         const int cn = min(ch, nchans - c0);
         const Tin *srow = rows + (size_t)buf * stage_elems;
@@ -329,7 +319,8 @@ __global__ void __launch_bounds__(NW * 32, 1) fast_kernel(FastLaunch a)
                                    bgoff + ((size_t)(c0 + cc) * NW + warp) * kDR);
         __syncthreads();
     }
-    if (!ok) return;
+    gstage = g0 + nst;
+    if (!ok) return false;
 
     // ---------------------------------------------------------------- epilogue
     const int64_t nout = a.nout;
@@ -395,6 +386,88 @@ __global__ void __launch_bounds__(NW * 32, 1) fast_kernel(FastLaunch a)
         }
         block_stat_f32(n, s, q, reinterpret_cast<StatF *>(a.partials) + lin);
     }
+    return true;
+}
+
+// Raster: DM blocks in groups of a.dgroup; within a group the time tiles
+// advance slowest, so concurrently resident blocks read nearby input spans
+// (better L2 reuse than sweeping all DM blocks of a tile at once).
+template <int TR>
+__device__ __forceinline__ void raster(const FastLaunch &a, int64_t lin, int &blk, int64_t &t0)
+{
+    const int64_t per_group = (int64_t)a.dgroup * a.ntile;
+    const int64_t grp = lin / per_group;
+    const int64_t rr = lin - grp * per_group;
+    const int gsize = min(a.dgroup, a.nblk - (int)grp * a.dgroup);
+    blk = (int)grp * a.dgroup + (int)(rr % gsize);
+    t0 = (rr / gsize) * (int64_t)(32 * TR);
+}
+
+// One plan: one block per work item, grid = nblk * ntile.
+template <typename Tin, bool kInt, int TR, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) fast_kernel(FastLaunch a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.bar_off);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int blk;
+    int64_t t0;
+    raster<TR>(a, blockIdx.x, blk, t0);
+    uint32_t gstage = 0;
+    process_tile<Tin, kInt, TR, NW>(a, blk, t0, blockIdx.x, smem, bar, gstage);
+}
+
+// Batched plans (uneven beams, mixed input types): a persistent grid pulls
+// work items (beam, linear tile index) from a device queue ordered heaviest
+// first, so beams of different channel counts and lengths share one launch.
+struct BatchLaunch {
+    const FastLaunch *beams;     // [nbeams], each with its own tables and buffers
+    const uint2 *items;          // [nitems] (beam, linear tile index within the beam)
+    int nitems;
+    int bar_off;
+    unsigned int *counter;       // work-queue head, zeroed before the launch
+    int *err;
+};
+
+template <int TR, int NW>
+__global__ void __launch_bounds__(NW * 32, 1) batch_kernel(BatchLaunch b)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_item;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + b.bar_off);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t gstage = 0;
+    while (true) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(b.counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= b.nitems) break;
+        const uint2 w = b.items[it];
+        const FastLaunch &a = b.beams[w.x];
+        int blk;
+        int64_t t0;
+        raster<TR>(a, w.y, blk, t0);
+        bool ok;
+        switch (a.dtype) {
+        case DD_F32: ok = process_tile<float, false, TR, NW>(a, blk, t0, w.y, smem, bar, gstage); break;
+        case DD_F16: ok = process_tile<__half, false, TR, NW>(a, blk, t0, w.y, smem, bar, gstage); break;
+        default: ok = process_tile<uint8_t, true, TR, NW>(a, blk, t0, w.y, smem, bar, gstage); break;
+        }
+        if (!ok) break;
+        // the epilogue's generic-proxy shared accesses must be ordered before
+        // the next item's TMA writes into the same bytes
+        __syncthreads();
+        if (threadIdx.x == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
 }
 
 // Launch one configuration for one input type.  Grid: nblk * ntile blocks.
@@ -416,7 +489,15 @@ cudaError_t fast_prepare_cfg(size_t optin)
     cudaError_t e = allow_max_dynamic_smem((const void *)fast_kernel<float, false, TR, NW>, optin);
     if (e == cudaSuccess) e = allow_max_dynamic_smem((const void *)fast_kernel<__half, false, TR, NW>, optin);
     if (e == cudaSuccess) e = allow_max_dynamic_smem((const void *)fast_kernel<uint8_t, true, TR, NW>, optin);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem((const void *)batch_kernel<TR, NW>, optin);
     return e;
+}
+
+template <int TR, int NW>
+cudaError_t batch_launch_cfg(const BatchLaunch &b, int grid, size_t smem, cudaStream_t s)
+{
+    batch_kernel<TR, NW><<<grid, NW * 32, smem, s>>>(b);
+    return cudaGetLastError();
 }
 
 // Configurations compiled into the library: {samples per thread, warps}.
@@ -430,5 +511,8 @@ cudaError_t fast_launch_t28w8(dd_dtype t, const FastLaunch &a, cudaStream_t s);
 cudaError_t fast_prepare_t36w8(size_t optin);
 cudaError_t fast_prepare_t20w12(size_t optin);
 cudaError_t fast_prepare_t28w8(size_t optin);
+cudaError_t batch_launch_t36w8(const BatchLaunch &b, int grid, size_t smem, cudaStream_t s);
+cudaError_t batch_launch_t20w12(const BatchLaunch &b, int grid, size_t smem, cudaStream_t s);
+cudaError_t batch_launch_t28w8(const BatchLaunch &b, int grid, size_t smem, cudaStream_t s);
 
 }  // namespace dd

@@ -10,4 +10,9 @@ cudaError_t fast_launch_t20w12(dd_dtype t, const FastLaunch &a, cudaStream_t s)
 
 cudaError_t fast_prepare_t20w12(size_t optin) { return fast_prepare_cfg<20, 12>(optin); }
 
+cudaError_t batch_launch_t20w12(const BatchLaunch &b, int grid, size_t smem, cudaStream_t s)
+{
+    return batch_launch_cfg<20, 12>(b, grid, smem, s);
+}
+
 }  // namespace dd

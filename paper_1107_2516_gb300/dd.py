@@ -28,7 +28,9 @@ assert CANDIDATE_DTYPE.itemsize == 32
 EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "dd_search",
            "dd_last_stats", "dd_process_host", "dd_plan_set_kernel", "dd_plan_get_kernel",
            "dd_plan_autotune", "dd_plan_set_tile", "dd_plan_get_tile",
-           "dd_stats_f32_noalloc", "dd_last_error", "dd_version")
+           "dd_stats_f32_noalloc", "dd_last_error", "dd_version",
+           "dd_batch_create", "dd_batch_destroy", "dd_batch_execute", "dd_batch_capture",
+           "dd_batch_launch", "dd_batch_results", "dd_batch_autotune", "dd_batch_info")
 
 
 class DDError(RuntimeError):
@@ -68,6 +70,14 @@ def load(path: Optional[str] = None):
             "dd_plan_autotune": (C.c_int, [vp, vp, i64, vp, vp]),
             "dd_plan_set_tile": (C.c_int, [vp, i32, i32]),
             "dd_stats_f32_noalloc": (C.c_int, [vp, i64, vp, vp]),
+            "dd_batch_create": (C.c_int, [vp, i32, C.POINTER(vp)]),
+            "dd_batch_destroy": (C.c_int, [vp]),
+            "dd_batch_execute": (C.c_int, [vp, vp, vp, vp, vp]),
+            "dd_batch_capture": (C.c_int, [vp, vp, vp, vp, vp]),
+            "dd_batch_launch": (C.c_int, [vp, vp]),
+            "dd_batch_results": (C.c_int, [vp, i32, vp, i64, P64, vp]),
+            "dd_batch_autotune": (C.c_int, [vp, vp, vp, vp, vp]),
+            "dd_batch_info": (C.c_int, [vp, C.POINTER(i32), P64, C.POINTER(i32)]),
             "dd_plan_get_tile": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                            C.POINTER(i32)]),
             "dd_last_error": (C.c_char_p, []),
@@ -207,6 +217,100 @@ def dd_stats_f32_noalloc(x_dev, n: int, mu_sigma_dev, stream=None) -> None:
     (device, float64) without any allocation; for callers that cannot allocate
     device memory after start-up.  At most 2**28 values; see include/dd.h."""
     _check(load().dd_stats_f32_noalloc(_ptr(x_dev), int(n), _ptr(mu_sigma_dev), _stream(stream)))
+
+
+def _ptr_array(xs):
+    arr = (C.c_void_p * len(xs))(*[_ptr(x) for x in xs])
+    return arr
+
+
+def dd_batch_create(plans) -> int:
+    handles = (C.c_void_p * len(plans))(*[p.handle if isinstance(p, Plan) else int(p) for p in plans])
+    out = C.c_void_p()
+    _check(load().dd_batch_create(handles, len(plans), C.byref(out)))
+    return int(out.value)
+
+
+def dd_batch_destroy(batch: int) -> None:
+    _check(load().dd_batch_destroy(batch))
+
+
+def _batch_bufs(ins, pitches, outs):
+    p = (C.c_int64 * len(pitches))(*[int(v) for v in pitches])
+    return _ptr_array(ins), p, _ptr_array(outs)
+
+
+def dd_batch_execute(batch: int, ins, pitches, outs, stream=None) -> None:
+    a, p, o = _batch_bufs(ins, pitches, outs)
+    _check(load().dd_batch_execute(batch, a, p, o, _stream(stream)))
+
+
+def dd_batch_capture(batch: int, ins, pitches, outs, stream) -> None:
+    a, p, o = _batch_bufs(ins, pitches, outs)
+    _check(load().dd_batch_capture(batch, a, p, o, _stream(stream)))
+
+
+def dd_batch_launch(batch: int, stream) -> None:
+    _check(load().dd_batch_launch(batch, _stream(stream)))
+
+
+def dd_batch_results(batch: int, beam: int, capacity: int = 1 << 16, stream=None, allow_overflow=False):
+    cands = np.zeros(max(capacity, 1), dtype=CANDIDATE_DTYPE)
+    n = C.c_int64()
+    _check(load().dd_batch_results(batch, int(beam), cands.ctypes.data, int(capacity), C.byref(n),
+                                   _stream(stream)), allow=(DD_ERR_OVERFLOW,) if allow_overflow else ())
+    total = int(n.value)
+    return cands[:min(total, capacity)].copy(), total
+
+
+def dd_batch_autotune(batch: int, ins, pitches, outs, stream=None) -> None:
+    a, p, o = _batch_bufs(ins, pitches, outs)
+    _check(load().dd_batch_autotune(batch, a, p, o, _stream(stream)))
+
+
+def dd_batch_info(batch: int):
+    """(tile configuration of the persistent launch, work items, beams run separately)."""
+    c, n, s = C.c_int32(), C.c_int64(), C.c_int32()
+    _check(load().dd_batch_info(batch, C.byref(c), C.byref(n), C.byref(s)))
+    return int(c.value), int(n.value), int(s.value)
+
+
+class Batch:
+    """Owning wrapper around a dd_batch handle; keeps its plans alive."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        self.handle = dd_batch_create(self.plans)
+
+    def execute(self, ins, pitches, outs, stream=None):
+        dd_batch_execute(self.handle, ins, pitches, outs, stream)
+
+    def capture(self, ins, pitches, outs, stream):
+        dd_batch_capture(self.handle, ins, pitches, outs, stream)
+
+    def launch(self, stream):
+        dd_batch_launch(self.handle, stream)
+
+    def results(self, beam, capacity=1 << 16, stream=None, allow_overflow=False):
+        return dd_batch_results(self.handle, beam, capacity, stream, allow_overflow)
+
+    def autotune(self, ins, pitches, outs, stream=None):
+        dd_batch_autotune(self.handle, ins, pitches, outs, stream)
+
+    @property
+    def info(self):
+        return dd_batch_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            dd_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------- convenience object

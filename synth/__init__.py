@@ -150,3 +150,59 @@ def draw_pulses(n: int, dm_lo: float, dm_hi: float, width_lo: int, width_hi: int
         taken.append(t0)
         out.append(Pulse(dm=dm, t0=t0, width=w, amp=pulse_amplitude(snr, nchans, w)))
     return out
+
+
+@dataclasses.dataclass(frozen=True)
+class Beam:
+    """One beam of a batched or served workload (units as Workload)."""
+    nchans: int
+    fch1: float
+    foff: float
+    tsamp: float
+    nsamp: int
+    ndm: int
+    dm_step: float
+    dtype: str          # "f32" or "u8"
+    seed: int
+
+    @property
+    def dm_list(self) -> np.ndarray:
+        return np.arange(self.ndm, dtype=np.float64) * self.dm_step
+
+
+def batch_beams(n: int, seed: int, maxshift_of: Callable[[int, float, float, float, float], int],
+                mini: bool = False) -> List[Beam]:
+    """Uneven beams for the batched workload.
+
+    Full recipe: channels cycle {256, 512, 1024, 4096}; nsamp = 2^(16 + (7i mod 5));
+    fch1 ~ U(120, 1500) MHz; bandwidth ~ U(6, 300) MHz capped at fch1/2;
+    tsamp in {64, 81.92, 163.84, 327.68} us; DM trials ~ U{500..4000} with a
+    log-uniform step in [0.01, 0.5]; the number of trials is reduced (not
+    below 500) and then the step, until the maximum delay fits in half the
+    input.  Even beams float32, odd beams uint8.  `mini` shrinks every size for
+    tests (channels {64, 128, 256, 512}, nsamp 2^(13 + (7i mod 3)), 40..200 trials).
+    maxshift_of(nchans, fch1, foff, tsamp, dm_max) must return the plan's
+    maximum delay in samples (the caller supplies the delay law).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    chans = (64, 128, 256, 512) if mini else (256, 512, 1024, 4096)
+    tsamps = (64e-6, 81.92e-6, 163.84e-6, 327.68e-6)
+    out: List[Beam] = []
+    for i in range(n):
+        c = chans[i % len(chans)]
+        nsamp = 1 << ((13 + (7 * i) % 3) if mini else (16 + (7 * i) % 5))
+        fch1 = float(rng.uniform(120.0, 1500.0))
+        bw = min(float(rng.uniform(6.0, 300.0)), 0.5 * fch1)
+        ts = float(tsamps[int(rng.integers(0, 4))])
+        lo, hi = (40, 200) if mini else (500, 4000)
+        ndm = int(rng.integers(lo, hi + 1))
+        step = float(np.exp(rng.uniform(np.log(0.01), np.log(0.5))))
+        foff = -bw / c
+        while maxshift_of(c, fch1, foff, ts, (ndm - 1) * step) > nsamp // 2:
+            if ndm > lo:
+                ndm = max(lo, int(ndm * 0.8))
+            else:
+                step *= 0.8
+        out.append(Beam(nchans=c, fch1=fch1, foff=foff, tsamp=ts, nsamp=nsamp, ndm=ndm, dm_step=step,
+                        dtype="f32" if i % 2 == 0 else "u8", seed=seed * 1000 + i))
+    return out

@@ -1,0 +1,125 @@
+"""Batched beams (one persistent launch for uneven beams, mixed float32/uint8):
+every beam's output and candidate list equal what its plan alone produces, the
+CUDA-graph replay equals the direct launch, and small beams match the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from ddhelpers import compare_candidates, fp_tol, keys
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1107_2516_gb300 as dd
+from paper_1107_2516_gb300 import build as ddbuild
+
+WIDTHS = (1, 2, 4, 8)
+SIGMA = 5.0
+
+
+def maxshift_of(c, f1, fo, ts, dm):
+    return oracle.delays(c, f1, fo, ts, [dm])[1]
+
+
+@pytest.fixture(scope="module")
+def beams():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ddbuild.build()
+    bs = synth.batch_beams(6, 4, maxshift_of, mini=True)
+    data = []
+    for b in bs:
+        pitch = synth.aligned_pitch(b.nsamp, 4 if b.dtype == "f32" else 1)
+        x = synth.noise_f32(b.nchans, b.nsamp, b.seed, pitch=pitch)
+        d1, _ = oracle.delays(b.nchans, b.fch1, b.foff, b.tsamp, [float(b.dm_list[b.ndm // 2])])
+        p = synth.Pulse(dm=float(b.dm_list[b.ndm // 2]), t0=b.nsamp // 4, width=4,
+                        amp=synth.pulse_amplitude(15.0, b.nchans, 4))
+        synth.inject_pulses(x, [p], lambda dm: d1[0], b.nsamp)
+        arr = x if b.dtype == "f32" else synth.quantize_u8(x)
+        data.append((b, arr, pitch))
+    return data
+
+
+def _plans(data, cfg=None):
+    plans = []
+    for b, arr, pitch in data:
+        p = dd.Plan(b.nchans, b.fch1, b.foff, b.tsamp, b.dm_list, WIDTHS, SIGMA,
+                    dd.DD_F32 if b.dtype == "f32" else dd.DD_U8, b.nsamp)
+        if cfg is not None:
+            p.set_tile(cfg, 8)
+        plans.append(p)
+    return plans
+
+
+def _bufs(data, plans):
+    ins = [torch.from_numpy(arr).cuda() for _, arr, _ in data]
+    outs = [torch.empty(p.ndm * p.nsamp_out, dtype=torch.int32 if p.out_is_int else torch.float32,
+                        device="cuda") for p in plans]
+    return ins, [pitch for _, _, pitch in data], outs
+
+
+def test_batch_matches_single_plans_and_graph(beams):
+    plans = _plans(beams)
+    batch = dd.Batch(plans)
+    cfg, nitems, nsep = batch.info
+    assert cfg >= 0 and nitems > 0 and nsep == 0
+    for p in plans:
+        p.set_tile(cfg, 8)
+    ins, pitches, outs = _bufs(beams, plans)
+    # each plan alone
+    single = []
+    for p, x, pitch, o in zip(plans, ins, pitches, outs):
+        p.execute(x, pitch, o)
+        c, n = p.search(o)
+        single.append((o.clone(), c, n))
+    # one persistent launch for all beams
+    for o in outs:
+        o.zero_()
+    batch.execute(ins, pitches, outs)
+    for i, (o_ref, c_ref, n_ref) in enumerate(single):
+        c, n = batch.results(i)
+        assert torch.equal(outs[i], o_ref), f"beam {i} output differs"
+        assert n == n_ref and keys(c) == keys(c_ref)
+    # CUDA graph capture + replay
+    s = torch.cuda.Stream()
+    for o in outs:
+        o.zero_()
+    batch.capture(ins, pitches, outs, s)
+    for rep in range(2):
+        batch.launch(s)
+        for i, (o_ref, c_ref, n_ref) in enumerate(single):
+            c, n = batch.results(i, stream=s)
+            assert torch.equal(outs[i], o_ref)
+            assert n == n_ref and keys(c) == keys(c_ref)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
+def test_batch_beams_match_oracle(beams):
+    plans = _plans(beams)
+    batch = dd.Batch(plans)
+    ins, pitches, outs = _bufs(beams, plans)
+    batch.autotune(ins, pitches, outs)
+    batch.execute(ins, pitches, outs)
+    torch.cuda.synchronize()
+    for i, ((b, arr, pitch), p) in enumerate(zip(beams, plans)):
+        d, m = oracle.delays(b.nchans, b.fch1, b.foff, b.tsamp, b.dm_list)
+        nout = b.nsamp - m
+        assert p.nsamp_out == nout
+        ora = oracle.dedisperse(arr, d, nout)
+        got = outs[i].cpu().numpy().reshape(b.ndm, nout)
+        if b.dtype == "u8":
+            assert np.array_equal(got.astype(np.int64), ora)
+        else:
+            assert np.max(np.abs(got - ora)) <= fp_tol(b.nchans)
+        c, n = batch.results(i)
+        mu_g, sg_g = p.stats()
+        mu_o, sg_o = oracle.stats(ora)
+        res = compare_candidates(c, ora, list(WIDTHS), mu_g, sg_g, mu_o, sg_o, SIGMA,
+                                 0.0 if b.dtype == "u8" else fp_tol(b.nchans))
+        assert res[1] <= 2
+    batch.close()
+    for p in plans:
+        p.close()
