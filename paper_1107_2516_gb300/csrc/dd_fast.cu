@@ -132,6 +132,10 @@ static int build_cfg(const dd_plan *p, int tr, int nw, FastCfgData &c)
     const size_t smem = bar_off + kStages * sizeof(uint64_t);
     if (smem > budget + 1024) return DD_OK;
     c.nblk = nblk; c.rs = rs; c.ch = ch; c.bar_off = (int)bar_off; c.smem = smem;
+    // the fallback offsets are only read for descriptors marked generic
+    bool any_generic = false;
+    for (uint32_t dd : desc) any_generic |= ((dd >> 12) & 0xffu) == (uint32_t)kGeneric;
+    if (!any_generic) goff.assign(kDR, 0);
     cudaError_t e = cudaMalloc(&c.d_desc, desc.size() * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_base, base.size() * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_goff, goff.size() * 4);
