@@ -69,8 +69,24 @@ typedef enum {
     DD_ERR_CUDA = 3,      /* a CUDA runtime call failed                      */
     DD_ERR_OVERFLOW = 4,  /* more candidates than the caller's capacity      */
     DD_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up              */
-    DD_ERR_BUDGET = 6     /* admission refused: the HBM budget is exhausted  */
+    DD_ERR_BUDGET = 6,    /* admission refused: the HBM budget is exhausted  */
+    DD_PRIMING = 7        /* server chunk accepted, no output yet: the beam's
+                             resident history holds < maxshift samples       */
 } dd_status;
+
+typedef struct dd_server dd_server;
+
+/* Completion record of one served chunk (host steady-clock seconds). */
+typedef struct {
+    int32_t beam;
+    int32_t status;       /* DD_OK, DD_PRIMING or an error status            */
+    int64_t seq;          /* the caller's sequence number of the chunk       */
+    int64_t n_candidates; /* search hits of this chunk                       */
+    double t_submit;      /* dd_server_submit returned                       */
+    double t_start;       /* a worker took the chunk                         */
+    double t_done;        /* candidates on the host                          */
+    double mu, sigma;     /* statistics of this chunk's output               */
+} dd_chunk_result;
 
 /* One search hit (32 bytes).  value is B_w exactly as summed on the device
  * (an integer for DD_U8 plans); snr as defined above, in double, rounded to
@@ -216,6 +232,66 @@ DD_API int dd_batch_autotune(dd_batch *batch, const void *const *in_devs, const 
 /* Tile configuration the persistent launch uses (-1 if no beam uses it),
  * number of work items, and number of beams run by their own launch. */
 DD_API int dd_batch_info(const dd_batch *batch, int32_t *config, int64_t *nitems, int32_t *n_separate);
+
+/* ---------------------------------------------------------------------
+ * Streaming server.  The paper processes an unbounded stream buffer by
+ * buffer and needs maxshift extra samples per buffer (Section 3, "Maximum
+ * shift"; real-time pipeline, Section 5).  A server keeps, per beam, the last
+ * maxshift samples resident on the device, so each chunk of `chunk` new
+ * samples yields `chunk` de-dispersed samples per DM trial (stream output
+ * times [k*chunk - maxshift, (k+1)*chunk - maxshift) for chunk k) followed by
+ * a Section 3 search over them (statistics per chunk).  The first
+ * ceil(maxshift/chunk) chunks of a beam only fill the history (DD_PRIMING).
+ * Worker threads, each with its own CUDA stream, take the oldest ready chunk
+ * of any beam as soon as they are free, so chunks of different beams overlap
+ * on the device; chunks of one beam run in submission order.
+ * ------------------------------------------------------------------- */
+
+/* Create a server with `nworkers` worker threads/streams, a device-memory
+ * budget for admitted beams, and room for `max_candidates` hits per chunk. */
+DD_API int dd_server_create(int64_t hbm_budget_bytes, int32_t nworkers, int64_t max_candidates,
+                            dd_server **server_out);
+
+/* Stop the workers (after the chunk each is running) and free every beam. */
+DD_API int dd_server_destroy(dd_server *server);
+
+/* Admit a beam (plan parameters as dd_plan_create, `chunk` new samples per
+ * submission).  The beam's device memory (two history rings of
+ * nchans x (maxshift + chunk) samples, the output, the plan) is reserved
+ * against the budget: DD_ERR_BUDGET if it does not fit (nothing allocated). */
+DD_API int dd_server_add_beam(dd_server *server, int32_t nchans, double fch1_mhz, double foff_mhz,
+                              double tsamp_s, const double *dm_list, int32_t ndm,
+                              const int32_t *boxcar_widths, int32_t nwidths, double sigma_k,
+                              int32_t in_dtype, int64_t chunk, int32_t *beam_id);
+
+/* Remove a beam; its memory returns to the budget once its running chunk (if
+ * any) finishes.  Queued chunks of the beam are dropped. */
+DD_API int dd_server_remove_beam(dd_server *server, int32_t beam);
+
+/* Queue one chunk: chunk_host holds nchans rows of `chunk` samples,
+ * host_pitch elements apart (pinned or pageable).  It must stay valid and
+ * unchanged until dd_server_poll reports the chunk.  Returns immediately. */
+DD_API int dd_server_submit(dd_server *server, int32_t beam, const void *chunk_host, int64_t host_pitch,
+                            int64_t seq);
+
+/* Collect up to max_results completion records (waiting up to wait_ms for
+ * the first one). */
+DD_API int dd_server_poll(dd_server *server, dd_chunk_result *results, int32_t max_results, int32_t *n,
+                          int32_t wait_ms);
+
+/* Candidates of a completed chunk, sorted as dd_search returns them (the
+ * server keeps them until fetched). */
+DD_API int dd_server_candidates(dd_server *server, int32_t beam, int64_t seq, dd_candidate *cand_host,
+                                int64_t capacity, int64_t *n_found);
+
+/* A beam's maxshift, chunk, DM trials, reserved bytes and its device output
+ * buffer ([ndm][chunk], the latest completed chunk's; overwritten when the
+ * beam's next chunk runs).  Any output pointer may be NULL. */
+DD_API int dd_server_beam_info(dd_server *server, int32_t beam, int64_t *maxshift, int64_t *chunk,
+                               int64_t *ndm, void **out_dev, int64_t *device_bytes);
+
+/* Bytes reserved by admitted beams and the budget. */
+DD_API int dd_server_memory(dd_server *server, int64_t *used, int64_t *budget);
 
 /* Allocation-free statistics (no counterpart in the paper).  For callers that
  * cannot call cudaMalloc — e.g. a real-time pipeline whose device memory is

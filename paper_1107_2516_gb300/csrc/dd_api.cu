@@ -48,6 +48,21 @@ static long long delay_samples(double fch1, double foff, int nchans, double tsam
     return llround((k * diff) / tsamp_ms);
 }
 
+// Largest delay over all channels at the deepest DM trial (the plan's
+// maxshift), without building a plan; -1 for invalid arguments.
+long long max_delay(int nchans, double fch1, double foff, double tsamp_s, const double *dm_list, int ndm)
+{
+    if (nchans < 1 || ndm < 1 || !dm_list || !(tsamp_s > 0.0)) return -1;
+    double dmax = 0.0;
+    for (int i = 0; i < ndm; ++i) {
+        if (!(dm_list[i] >= 0.0)) return -1;
+        dmax = std::max(dmax, dm_list[i]);
+    }
+    long long m = 0;
+    for (int c = 0; c < nchans; ++c) m = std::max(m, delay_samples(fch1, foff, nchans, tsamp_s, dmax, c));
+    return m;
+}
+
 static void free_plan(dd_plan *p)
 {
     if (!p) return;

@@ -99,6 +99,7 @@ int generic_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaSt
 int stats_from_out(dd_plan *p, const void *out, cudaStream_t s);
 int search_launch(dd_plan *p, const void *out, cudaStream_t s);
 int ensure_partials_public(dd_plan *p, int64_t n);
+long long max_delay(int nchans, double fch1, double foff, double tsamp_s, const double *dm_list, int ndm);
 int search_readback(dd_plan *plan, dd_candidate *cand_host, int64_t capacity, int64_t *n_found,
                     cudaStream_t s, int64_t dev_cap);
 cudaError_t allow_max_dynamic_smem(const void *fn, size_t optin);

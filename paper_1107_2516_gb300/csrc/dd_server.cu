@@ -1,0 +1,337 @@
+// Streaming server: beams submit chunks of new samples as they arrive; each
+// beam keeps the last maxshift samples of its stream resident on the device
+// (Section 3, "Maximum shift": n outputs need n + maxshift inputs), so every
+// chunk of N new samples yields N de-dispersed samples per DM trial and a
+// Section 3 search over them.  Worker threads, each with its own CUDA stream,
+// take the next ready chunk of any beam as soon as they are free, so chunks
+// that arrive while others are on the GPU start immediately and overlap on the
+// device (continuous batching).  Beams are admitted against a device-memory
+// budget.
+#include "dd_internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+namespace {
+
+double now_s()
+{
+    using namespace std::chrono;
+    return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct Pending {
+    int64_t seq;
+    const void *host;
+    int64_t host_pitch;
+    double t_submit;
+};
+
+struct ServerBeam {
+    int id = 0;
+    dd_plan *plan = nullptr;
+    int64_t chunk = 0, maxshift = 0, nin = 0, pitch = 0;
+    size_t eb = 1;
+    void *ring[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *out = nullptr;
+    int64_t processed = 0;
+    bool busy = false, removed = false;
+    std::deque<Pending> queue;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct dd_server {
+    int device = 0;
+    int64_t budget = 0, used = 0;
+    int64_t cand_cap = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::map<int, ServerBeam *> beams;
+    int next_id = 0;
+    std::vector<std::thread> workers;
+    std::vector<cudaStream_t> streams;
+    std::deque<dd_chunk_result> done;
+    std::map<std::pair<int, int64_t>, std::vector<dd_candidate>> cands;
+    bool stop = false;
+};
+
+namespace dd {
+
+static void free_beam(ServerBeam *b)
+{
+    if (b->plan) dd_plan_destroy(b->plan);
+    for (void *r : b->ring)
+        if (r) cudaFree(r);
+    if (b->out) cudaFree(b->out);
+    delete b;
+}
+
+// Next beam with a pending chunk and no chunk in flight (oldest submission first).
+static ServerBeam *pick(dd_server *S)
+{
+    ServerBeam *best = nullptr;
+    for (auto &kv : S->beams) {
+        ServerBeam *b = kv.second;
+        if (b->busy || b->removed || b->queue.empty()) continue;
+        if (!best || b->queue.front().t_submit < best->queue.front().t_submit) best = b;
+    }
+    return best;
+}
+
+static void process(dd_server *S, ServerBeam *b, const Pending &pc, cudaStream_t s, dd_chunk_result &r,
+                    std::vector<dd_candidate> &found)
+{
+    r.beam = b->id;
+    r.seq = pc.seq;
+    r.t_submit = pc.t_submit;
+    r.t_start = now_s();
+    r.status = DD_OK;
+    const int nxt = 1 - b->cur;
+    const size_t rowb = (size_t)b->pitch * b->eb;
+    // history: the last maxshift samples of the previous ring -> front of the next ring
+    cudaError_t e = cudaSuccess;
+    if (b->maxshift > 0)
+        e = cudaMemcpy2DAsync(b->ring[nxt], rowb, (const char *)b->ring[b->cur] + (size_t)b->chunk * b->eb, rowb,
+                              (size_t)b->maxshift * b->eb, (size_t)b->plan->nchans, cudaMemcpyDeviceToDevice, s);
+    // new samples behind it
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync((char *)b->ring[nxt] + (size_t)b->maxshift * b->eb, rowb, pc.host,
+                              (size_t)pc.host_pitch * b->eb, (size_t)b->chunk * b->eb, (size_t)b->plan->nchans,
+                              cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        r.status = cuda_fail(e, "server copies");
+    } else if (b->processed * b->chunk < b->maxshift) {
+        // the resident history does not yet hold maxshift real samples
+        e = cudaStreamSynchronize(s);
+        r.status = e == cudaSuccess ? DD_PRIMING : cuda_fail(e, "server sync");
+    } else {
+        int rc = dd_execute(b->plan, b->ring[nxt], b->pitch, b->out, s);
+        int64_t n = 0;
+        found.resize((size_t)S->cand_cap);
+        if (rc == DD_OK) rc = dd_search(b->plan, b->out, found.data(), S->cand_cap, &n, s);
+        found.resize((size_t)std::min(n, S->cand_cap));
+        r.status = rc;
+        r.n_candidates = n;
+        dd_last_stats(b->plan, &r.mu, &r.sigma);
+    }
+    b->cur = nxt;
+    b->processed++;
+    r.t_done = now_s();
+}
+
+static void worker(dd_server *S, int w)
+{
+    cudaSetDevice(S->device);
+    cudaStream_t s = S->streams[w];
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (true) {
+        ServerBeam *b = nullptr;
+        S->cv_work.wait(lk, [&] { return S->stop || (b = pick(S)) != nullptr; });
+        if (S->stop) return;
+        Pending pc = b->queue.front();
+        b->queue.pop_front();
+        b->busy = true;
+        lk.unlock();
+        dd_chunk_result r;
+        memset(&r, 0, sizeof(r));
+        std::vector<dd_candidate> found;
+        process(S, b, pc, s, r, found);
+        lk.lock();
+        b->busy = false;
+        if (!found.empty()) S->cands[{b->id, pc.seq}] = std::move(found);
+        S->done.push_back(r);
+        if (b->removed && b->queue.empty()) {
+            S->used -= (int64_t)b->bytes;
+            S->beams.erase(b->id);
+            free_beam(b);
+        }
+        S->cv_done.notify_all();
+        S->cv_work.notify_all();
+    }
+}
+
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" {
+
+int dd_server_create(int64_t hbm_budget_bytes, int32_t nworkers, int64_t max_candidates, dd_server **out)
+{
+    if (!out) return set_error(DD_ERR_ARG, "server_out is NULL");
+    *out = nullptr;
+    if (hbm_budget_bytes <= 0 || nworkers < 1 || nworkers > 64 || max_candidates < 1)
+        return set_error(DD_ERR_ARG, "bad server parameters");
+    dd_server *S = new dd_server();
+    cudaGetDevice(&S->device);
+    S->budget = hbm_budget_bytes;
+    S->cand_cap = max_candidates;
+    for (int w = 0; w < nworkers; ++w) {
+        cudaStream_t s;
+        cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { dd_server_destroy(S); return cuda_fail(e, "cudaStreamCreate"); }
+        S->streams.push_back(s);
+    }
+    for (int w = 0; w < nworkers; ++w) S->workers.emplace_back(worker, S, w);
+    *out = S;
+    return DD_OK;
+}
+
+int dd_server_destroy(dd_server *S)
+{
+    if (!S) return DD_OK;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    for (auto &t : S->workers) t.join();
+    for (auto &kv : S->beams) free_beam(kv.second);
+    for (cudaStream_t s : S->streams) cudaStreamDestroy(s);
+    delete S;
+    return DD_OK;
+}
+
+int dd_server_add_beam(dd_server *S, int32_t nchans, double fch1, double foff, double tsamp,
+                       const double *dm_list, int32_t ndm, const int32_t *widths, int32_t nwidths,
+                       double sigma, int32_t dtype, int64_t chunk, int32_t *beam_id)
+{
+    if (!S || !beam_id || chunk < 1) return set_error(DD_ERR_ARG, "bad arguments");
+    cudaSetDevice(S->device);
+    // maxshift first: it sizes the history ring and the plan's input length
+    const long long M = max_delay(nchans, fch1, foff, tsamp, dm_list, ndm);
+    if (M < 0) return set_error(DD_ERR_ARG, "invalid beam parameters");
+    if (dtype != DD_F32 && dtype != DD_U8 && dtype != DD_F16) return set_error(DD_ERR_ARG, "unknown input dtype");
+    int rc = DD_OK;
+    const size_t eb = in_elem_bytes((dd_dtype)dtype);
+    const int64_t nin = M + chunk;
+    const int64_t al = 16 / (int64_t)eb;
+    const int64_t pitch = (nin + al - 1) / al * al;
+    // device bytes: two rings, the output, and the plan's tables (delay-table sized estimate)
+    const size_t ring_b = (size_t)nchans * (size_t)pitch * eb;
+    const size_t out_b = (size_t)ndm * (size_t)chunk * 4;
+    const size_t tab_b = (size_t)ndm * (size_t)nchans * 4 * 8;
+    const size_t need = 2 * ring_b + out_b + tab_b;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        if (S->used + (int64_t)need > S->budget)
+            return set_error(DD_ERR_BUDGET, "admission refused: beam needs %zu bytes, %lld of %lld in use",
+                             need, (long long)S->used, (long long)S->budget);
+        S->used += (int64_t)need;    // reserve before allocating
+    }
+    ServerBeam *b = new ServerBeam();
+    b->chunk = chunk; b->maxshift = M; b->nin = nin; b->pitch = pitch; b->eb = eb; b->bytes = need;
+    rc = dd_plan_create(nchans, fch1, foff, tsamp, dm_list, ndm, widths, nwidths, sigma, dtype, nin, &b->plan);
+    cudaError_t e = cudaSuccess;
+    if (rc == DD_OK) e = cudaMalloc(&b->ring[0], ring_b);
+    if (rc == DD_OK && e == cudaSuccess) e = cudaMalloc(&b->ring[1], ring_b);
+    if (rc == DD_OK && e == cudaSuccess) e = cudaMalloc(&b->out, out_b);
+    if (rc == DD_OK && e == cudaSuccess) e = cudaMemset(b->ring[0], 0, ring_b);
+    if (rc == DD_OK && e != cudaSuccess) rc = cuda_fail(e, "beam buffers");
+    std::lock_guard<std::mutex> g(S->mu);
+    if (rc != DD_OK) {
+        S->used -= (int64_t)need;
+        free_beam(b);
+        return rc;
+    }
+    b->id = S->next_id++;
+    S->beams[b->id] = b;
+    *beam_id = b->id;
+    return DD_OK;
+}
+
+int dd_server_remove_beam(dd_server *S, int32_t beam)
+{
+    if (!S) return set_error(DD_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->beams.find(beam);
+    if (it == S->beams.end()) return set_error(DD_ERR_ARG, "no beam %d", beam);
+    ServerBeam *b = it->second;
+    b->removed = true;
+    b->queue.clear();
+    if (!b->busy) {
+        S->used -= (int64_t)b->bytes;
+        S->beams.erase(it);
+        free_beam(b);
+    }
+    return DD_OK;
+}
+
+int dd_server_submit(dd_server *S, int32_t beam, const void *chunk_host, int64_t host_pitch, int64_t seq)
+{
+    if (!S || !chunk_host) return set_error(DD_ERR_ARG, "bad arguments");
+    const double t = now_s();
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->beams.find(beam);
+    if (it == S->beams.end() || it->second->removed) return set_error(DD_ERR_ARG, "no beam %d", beam);
+    if (host_pitch < it->second->chunk) return set_error(DD_ERR_ARG, "host_pitch < chunk");
+    it->second->queue.push_back(Pending{seq, chunk_host, host_pitch, t});
+    S->cv_work.notify_one();
+    return DD_OK;
+}
+
+int dd_server_poll(dd_server *S, dd_chunk_result *results, int32_t max_results, int32_t *n, int32_t wait_ms)
+{
+    if (!S || !n || (max_results > 0 && !results)) return set_error(DD_ERR_ARG, "bad arguments");
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->done.empty() && wait_ms > 0)
+        S->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), [&] { return !S->done.empty(); });
+    int k = 0;
+    while (k < max_results && !S->done.empty()) {
+        results[k++] = S->done.front();
+        S->done.pop_front();
+    }
+    *n = k;
+    return DD_OK;
+}
+
+int dd_server_candidates(dd_server *S, int32_t beam, int64_t seq, dd_candidate *cand_host, int64_t capacity,
+                         int64_t *n_found)
+{
+    if (!S || !n_found || capacity < 0 || (capacity > 0 && !cand_host)) return set_error(DD_ERR_ARG, "bad arguments");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->cands.find({beam, seq});
+    if (it == S->cands.end()) { *n_found = 0; return DD_OK; }
+    const int64_t n = (int64_t)it->second.size();
+    memcpy(cand_host, it->second.data(), (size_t)std::min(n, capacity) * sizeof(dd_candidate));
+    *n_found = n;
+    S->cands.erase(it);
+    return n > capacity ? set_error(DD_ERR_OVERFLOW, "capacity too small") : DD_OK;
+}
+
+int dd_server_beam_info(dd_server *S, int32_t beam, int64_t *maxshift, int64_t *chunk, int64_t *ndm,
+                        void **out_dev, int64_t *device_bytes)
+{
+    if (!S) return set_error(DD_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->beams.find(beam);
+    if (it == S->beams.end()) return set_error(DD_ERR_ARG, "no beam %d", beam);
+    ServerBeam *b = it->second;
+    if (maxshift) *maxshift = b->maxshift;
+    if (chunk) *chunk = b->chunk;
+    if (ndm) *ndm = b->plan->ndm;
+    if (out_dev) *out_dev = b->out;
+    if (device_bytes) *device_bytes = (int64_t)b->bytes;
+    return DD_OK;
+}
+
+int dd_server_memory(dd_server *S, int64_t *used, int64_t *budget)
+{
+    if (!S) return set_error(DD_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> g(S->mu);
+    if (used) *used = S->used;
+    if (budget) *budget = S->budget;
+    return DD_OK;
+}
+
+}  // extern "C"

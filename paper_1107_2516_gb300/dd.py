@@ -30,7 +30,18 @@ EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "d
            "dd_plan_autotune", "dd_plan_set_tile", "dd_plan_get_tile",
            "dd_stats_f32_noalloc", "dd_last_error", "dd_version",
            "dd_batch_create", "dd_batch_destroy", "dd_batch_execute", "dd_batch_capture",
-           "dd_batch_launch", "dd_batch_results", "dd_batch_autotune", "dd_batch_info")
+           "dd_batch_launch", "dd_batch_results", "dd_batch_autotune", "dd_batch_info",
+           "dd_server_create", "dd_server_destroy", "dd_server_add_beam", "dd_server_remove_beam",
+           "dd_server_submit", "dd_server_poll", "dd_server_candidates", "dd_server_beam_info",
+           "dd_server_memory")
+
+DD_PRIMING = 7
+
+CHUNK_RESULT_DTYPE = np.dtype([("beam", np.int32), ("status", np.int32), ("seq", np.int64),
+                               ("n_candidates", np.int64), ("t_submit", np.float64),
+                               ("t_start", np.float64), ("t_done", np.float64),
+                               ("mu", np.float64), ("sigma", np.float64)])
+assert CHUNK_RESULT_DTYPE.itemsize == 64
 
 
 class DDError(RuntimeError):
@@ -78,6 +89,16 @@ def load(path: Optional[str] = None):
             "dd_batch_results": (C.c_int, [vp, i32, vp, i64, P64, vp]),
             "dd_batch_autotune": (C.c_int, [vp, vp, vp, vp, vp]),
             "dd_batch_info": (C.c_int, [vp, C.POINTER(i32), P64, C.POINTER(i32)]),
+            "dd_server_create": (C.c_int, [i64, i32, i64, C.POINTER(vp)]),
+            "dd_server_destroy": (C.c_int, [vp]),
+            "dd_server_add_beam": (C.c_int, [vp, i32, f64, f64, f64, vp, i32, vp, i32, f64, i32, i64,
+                                             C.POINTER(i32)]),
+            "dd_server_remove_beam": (C.c_int, [vp, i32]),
+            "dd_server_submit": (C.c_int, [vp, i32, vp, i64, i64]),
+            "dd_server_poll": (C.c_int, [vp, vp, i32, C.POINTER(i32), i32]),
+            "dd_server_candidates": (C.c_int, [vp, i32, i64, vp, i64, P64]),
+            "dd_server_beam_info": (C.c_int, [vp, i32, P64, P64, P64, C.POINTER(vp), P64]),
+            "dd_server_memory": (C.c_int, [vp, P64, P64]),
             "dd_plan_get_tile": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                            C.POINTER(i32)]),
             "dd_last_error": (C.c_char_p, []),
@@ -273,6 +294,79 @@ def dd_batch_info(batch: int):
     c, n, s = C.c_int32(), C.c_int64(), C.c_int32()
     _check(load().dd_batch_info(batch, C.byref(c), C.byref(n), C.byref(s)))
     return int(c.value), int(n.value), int(s.value)
+
+
+class Server:
+    """Owning wrapper around a dd_server handle (marshalling only)."""
+
+    def __init__(self, hbm_budget_bytes: int, nworkers: int = 4, max_candidates: int = 1 << 16):
+        out = C.c_void_p()
+        _check(load().dd_server_create(int(hbm_budget_bytes), int(nworkers), int(max_candidates),
+                                       C.byref(out)))
+        self.handle = int(out.value)
+        self._keep = {}
+
+    def add_beam(self, nchans, fch1, foff, tsamp, dm_list, widths, sigma, in_dtype, chunk) -> int:
+        """Beam id; raises DDError(DD_ERR_BUDGET) if its memory does not fit the budget."""
+        dm = np.ascontiguousarray(np.asarray(dm_list, dtype=np.float64))
+        w = np.ascontiguousarray(np.asarray(widths, dtype=np.int32))
+        bid = C.c_int32()
+        _check(load().dd_server_add_beam(self.handle, int(nchans), float(fch1), float(foff),
+                                         float(tsamp), dm.ctypes.data, int(dm.size), w.ctypes.data,
+                                         int(w.size), float(sigma), int(in_dtype), int(chunk),
+                                         C.byref(bid)))
+        return int(bid.value)
+
+    def remove_beam(self, beam: int) -> None:
+        _check(load().dd_server_remove_beam(self.handle, int(beam)))
+
+    def submit(self, beam: int, chunk_host, host_pitch: int, seq: int) -> None:
+        """chunk_host must stay alive and unchanged until poll() reports (beam, seq)."""
+        self._keep[(int(beam), int(seq))] = chunk_host
+        _check(load().dd_server_submit(self.handle, int(beam), _ptr(chunk_host), int(host_pitch),
+                                       int(seq)))
+
+    def poll(self, max_results: int = 256, wait_ms: int = 0) -> np.ndarray:
+        res = np.zeros(max_results, dtype=CHUNK_RESULT_DTYPE)
+        n = C.c_int32()
+        _check(load().dd_server_poll(self.handle, res.ctypes.data, int(max_results), C.byref(n),
+                                     int(wait_ms)))
+        res = res[:n.value].copy()
+        for r in res:
+            self._keep.pop((int(r["beam"]), int(r["seq"])), None)
+        return res
+
+    def candidates(self, beam: int, seq: int, capacity: int = 1 << 16):
+        cands = np.zeros(max(capacity, 1), dtype=CANDIDATE_DTYPE)
+        n = C.c_int64()
+        _check(load().dd_server_candidates(self.handle, int(beam), int(seq), cands.ctypes.data,
+                                           int(capacity), C.byref(n)))
+        return cands[:min(int(n.value), capacity)].copy()
+
+    def beam_info(self, beam: int) -> dict:
+        m, ch, nd, nb = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
+        outp = C.c_void_p()
+        _check(load().dd_server_beam_info(self.handle, int(beam), C.byref(m), C.byref(ch),
+                                          C.byref(nd), C.byref(outp), C.byref(nb)))
+        return {"maxshift": int(m.value), "chunk": int(ch.value), "ndm": int(nd.value),
+                "out_dev": int(outp.value or 0), "device_bytes": int(nb.value)}
+
+    def memory(self):
+        u, b = C.c_int64(), C.c_int64()
+        _check(load().dd_server_memory(self.handle, C.byref(u), C.byref(b)))
+        return int(u.value), int(b.value)
+
+    def close(self):
+        if self.handle:
+            load().dd_server_destroy(self.handle)
+            self.handle = 0
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:
