@@ -411,14 +411,124 @@ def run_batch(args):
         p.close()
 
 
+def run_serve(args):
+    """64 streaming uint8 beams (1024/4096 channels, 1000-4096 DM trials to DM
+    500, chunks of 65536 samples) arriving at args.speed x the real-time rate
+    with +-10% jitter.  Beams are admitted against 60% of free device memory;
+    a beam that does not fit waits until a served beam leaves (each beam
+    streams its priming chunks + 3 searched chunks).  Prints one JSON line
+    (mode "serve") with throughput, p50/p99 chunk latency and real-time factor."""
+    import torch
+    import paper_1107_2516_gb300 as dd
+    from paper_1107_2516_gb300 import build as ddbuild
+
+    ddbuild.build()
+    dd.load()
+    beams = synth.serve_beams(64, 5)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.6 * free)
+    srv = dd.Server(budget, nworkers=args.workers, max_candidates=1 << 16)
+    data = {c: torch.from_numpy(synth.quantize_u8(synth.noise_f32(c, 65536, seed=c))).pin_memory()
+            for c in (1024, 4096)}
+    widths = (1, 2, 4, 8, 16, 32, 64)
+    pending = list(range(len(beams)))
+    active = {}            # beam index -> dict(id, times, next, total, done, real)
+    refused_first = 0
+    lat, proc, rtf, units = [], [], [], 0
+    t0 = time.perf_counter()
+    first_try = True
+
+    def admit(now):
+        nonlocal refused_first
+        still = []
+        for i in pending:
+            b = beams[i]
+            try:
+                bid = srv.add_beam(b.nchans, b.fch1, b.foff, b.tsamp, b.dm_list, widths, 6.0,
+                                   dd.DD_U8, b.chunk)
+            except dd.DDError as e:
+                if e.code != 6:
+                    raise
+                still.append(i)
+                continue
+            info = srv.beam_info(bid)
+            prime = -(-info["maxshift"] // b.chunk)
+            n = prime + 3
+            times = now + synth.arrival_times(b, n, b.seed) / args.speed
+            active[i] = dict(id=bid, times=times, next=0, total=n, done=0, real=0, ndm=b.ndm)
+        if first_try:
+            refused_first += len(still)
+        pending[:] = still
+
+    admit(0.0)
+    first_try = False
+    byid = {v["id"]: k for k, v in active.items()}
+    limit = args.serve_limit
+    while (active or pending) and time.perf_counter() - t0 < limit:
+        now = time.perf_counter() - t0
+        nxt = None
+        for i, st in active.items():
+            while st["next"] < st["total"] and st["times"][st["next"]] <= now:
+                srv.submit(st["id"], data[beams[i].nchans], beams[i].chunk, st["next"])
+                st["next"] += 1
+            if st["next"] < st["total"]:
+                ta = st["times"][st["next"]]
+                nxt = ta if nxt is None else min(nxt, ta)
+        wait = 50 if nxt is None else max(1, min(50, int((nxt - now) * 1000)))
+        for r in srv.poll(max_results=256, wait_ms=wait):
+            i = byid[int(r["beam"])]
+            st = active[i]
+            st["done"] += 1
+            if int(r["status"]) == 0:
+                lat.append(float(r["t_done"] - r["t_submit"]))
+                pt = float(r["t_done"] - r["t_start"])
+                proc.append(pt)
+                rtf.append(beams[i].period / pt)
+                units += st["ndm"] * beams[i].chunk
+                st["real"] += 1
+            elif int(r["status"]) != dd.DD_PRIMING:
+                raise RuntimeError(f"chunk failed with status {int(r['status'])}")
+            if st["done"] == st["total"]:
+                srv.remove_beam(st["id"])
+                del active[i]
+                if pending:
+                    admit(time.perf_counter() - t0)
+                    byid = {v["id"]: k for k, v in active.items()}
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat_a, rtf_a = np.array(lat), np.array(rtf)
+    line = {
+        "mode": "serve", "metric": METRIC, "value": units / wall, "unit": METRIC,
+        "n_gpus": 1, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "64 streaming uint8 beams, 1024/4096 ch, 1000-4096 DMs to DM 500, "
+                   "chunks of 65536 samples, widths 1..64, 6 sigma",
+                   "arrival": f"{args.speed}x real-time rate, +-10% jitter, random phase",
+                   "hbm_budget_bytes": budget, "workers": args.workers},
+        "chunks_searched": len(lat), "beams": len(beams),
+        "beams_refused_at_start_then_admitted": refused_first,
+        "beams_never_admitted": len(pending),
+        "latency_s": {"p50": float(np.percentile(lat_a, 50)) if len(lat) else None,
+                      "p99": float(np.percentile(lat_a, 99)) if len(lat) else None},
+        "processing_s": {"p50": float(np.percentile(proc, 50)) if proc else None},
+        "real_time_factor": {"median": float(np.median(rtf_a)) if len(rtf) else None,
+                             "min": float(rtf_a.min()) if len(rtf) else None},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="lofar", choices=["lofar", "batch"],
-                    help="lofar: the benchmark line; batch: the 24-beam batched workload")
+    ap.add_argument("--mode", default="lofar", choices=["lofar", "batch", "serve"],
+                    help="lofar: the benchmark line; batch: the 24-beam batched workload; "
+                         "serve: the 64-beam streaming workload")
+    ap.add_argument("--speed", type=float, default=4.0, help="serve: arrival rate / real-time rate")
+    ap.add_argument("--workers", type=int, default=4, help="serve: server worker streams")
+    ap.add_argument("--serve-limit", type=float, default=240.0, help="serve: wall-clock limit (s)")
     ap.add_argument("--kernel", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
@@ -431,6 +541,9 @@ def main():
         return
     if args.mode == "batch":
         run_batch(args)
+        return
+    if args.mode == "serve":
+        run_serve(args)
         return
     if world > 1:
         import torch

@@ -206,3 +206,56 @@ def batch_beams(n: int, seed: int, maxshift_of: Callable[[int, float, float, flo
         out.append(Beam(nchans=c, fch1=fch1, foff=foff, tsamp=ts, nsamp=nsamp, ndm=ndm, dm_step=step,
                         dtype="f32" if i % 2 == 0 else "u8", seed=seed * 1000 + i))
     return out
+
+
+@dataclasses.dataclass(frozen=True)
+class ServedBeam:
+    """One streaming beam: plan parameters, chunk size and arrival schedule."""
+    nchans: int
+    fch1: float
+    foff: float
+    tsamp: float
+    ndm: int
+    dm_max: float
+    chunk: int
+    dtype: str
+    phase: float        # first arrival, fraction of a chunk period
+    seed: int
+
+    @property
+    def dm_list(self) -> np.ndarray:
+        return np.arange(self.ndm, dtype=np.float64) * (self.dm_max / self.ndm)
+
+    @property
+    def period(self) -> float:
+        """Seconds of sky time per chunk (the real-time arrival interval)."""
+        return self.chunk * self.tsamp
+
+
+def serve_beams(n: int, seed: int) -> List[ServedBeam]:
+    """Streaming beams: channels alternate 1024/4096, uint8 samples; tsamp in
+    {64, 81.92, 163.84, 327.68} us; fch1 ~ U(300, 1500) MHz, bandwidth
+    ~ U(0.10, 0.25) fch1; 1000..4096 DM trials over [0, 500); chunks of 65536
+    samples with a random arrival phase."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tsamps = (64e-6, 81.92e-6, 163.84e-6, 327.68e-6)
+    out: List[ServedBeam] = []
+    for i in range(n):
+        c = 1024 if i % 2 == 0 else 4096
+        ts = float(tsamps[int(rng.integers(0, 4))])
+        fch1 = float(rng.uniform(300.0, 1500.0))
+        bw = float(rng.uniform(0.10, 0.25)) * fch1
+        ndm = int(rng.integers(1000, 4097))
+        out.append(ServedBeam(nchans=c, fch1=fch1, foff=-bw / c, tsamp=ts, ndm=ndm, dm_max=500.0,
+                              chunk=65536, dtype="u8", phase=float(rng.uniform(0.0, 1.0)),
+                              seed=seed * 1000 + i))
+    return out
+
+
+def arrival_times(beam: ServedBeam, nchunks: int, seed: int, jitter: float = 0.1) -> np.ndarray:
+    """Arrival time of each chunk (seconds from the start): one chunk period
+    apart, each interval scaled by U(1 - jitter, 1 + jitter)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gaps = beam.period * rng.uniform(1.0 - jitter, 1.0 + jitter, size=nchunks)
+    t = beam.phase * beam.period + np.concatenate([[0.0], np.cumsum(gaps[:-1])])
+    return t
