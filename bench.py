@@ -414,7 +414,7 @@ def run_batch(args):
 def run_serve(args):
     """64 streaming uint8 beams (1024/4096 channels, 1000-4096 DM trials to DM
     500, chunks of 65536 samples) arriving at args.speed x the real-time rate
-    with +-10% jitter.  Beams are admitted against 60% of free device memory;
+    with +-10% jitter.  Beams are admitted against args.budget_frac of free device memory;
     a beam that does not fit waits until a served beam leaves (each beam
     streams its priming chunks + 3 searched chunks).  Prints one JSON line
     (mode "serve") with throughput, p50/p99 chunk latency and real-time factor."""
@@ -426,7 +426,7 @@ def run_serve(args):
     dd.load()
     beams = synth.serve_beams(64, 5)
     free, _ = torch.cuda.mem_get_info()
-    budget = int(0.6 * free)
+    budget = int(args.budget_frac * free)
     srv = dd.Server(budget, nworkers=args.workers, max_candidates=1 << 16)
     data = {c: torch.from_numpy(synth.quantize_u8(synth.noise_f32(c, 65536, seed=c))).pin_memory()
             for c in (1024, 4096)}
@@ -529,6 +529,7 @@ def main():
     ap.add_argument("--speed", type=float, default=4.0, help="serve: arrival rate / real-time rate")
     ap.add_argument("--workers", type=int, default=4, help="serve: server worker streams")
     ap.add_argument("--serve-limit", type=float, default=240.0, help="serve: wall-clock limit (s)")
+    ap.add_argument("--budget-frac", type=float, default=0.6, help="serve: HBM budget / free memory")
     ap.add_argument("--kernel", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
