@@ -156,11 +156,14 @@ DD_API int dd_process_host(dd_plan *plan, const void *in_host, int64_t in_pitch,
                     void *stream);
 
 /* Select the de-dispersion kernel for a plan: 0 = automatic (default),
- * 1 = generic shared-memory kernel, 2 = register-blocked kernel.  Returns
- * DD_ERR_ARG if the requested kernel cannot run this plan. */
+ * 1 = generic shared-memory kernel, 2 = register-blocked kernel (window
+ * reused across 4 DM trials per thread), 3 = lane-interleaved kernel (one
+ * conflict-free shared load per add, no branches).  Kernels 2 and 3 share the
+ * tile-configuration list of dd_plan_set_tile.  Returns DD_ERR_ARG if the
+ * requested kernel cannot run this plan. */
 DD_API int dd_plan_set_kernel(dd_plan *plan, int32_t kernel);
 
-/* Kernel that dd_execute will launch for this plan (1 or 2, see above). */
+/* Kernel that dd_execute will launch for this plan (1, 2 or 3, see above). */
 DD_API int dd_plan_get_kernel(const dd_plan *plan, int32_t *kernel);
 
 /* Autotuner for the register-blocked kernel (kernel 2): runs the plan on the
@@ -174,8 +177,9 @@ DD_API int dd_plan_autotune(dd_plan *plan, const void *in_dev, int64_t in_pitch,
                             void *stream);
 
 /* Choose kernel 2's tile configuration explicitly.  config indexes the
- * compiled list {0: 36 samples x 4 DM trials per thread, 8 warps;
- * 1: 20 x 4, 12 warps; 2: 28 x 4, 8 warps}; raster_group (>= 1) is the
+ * compiled list {kernel 2 — 0: 36 samples x 4 DM trials per thread, 8 warps;
+ * 1: 20 x 4, 12 warps; 2: 28 x 4, 8 warps; kernel 3 — 3: 16 samples per
+ * lane x 4 DM trials per warp, 8 warps; 4: 16 x 8, 8 warps}; raster_group (>= 1) is the
  * number of DM blocks whose time tiles are swept together.  DD_ERR_ARG if
  * the configuration cannot run this plan. */
 DD_API int dd_plan_set_tile(dd_plan *plan, int32_t config, int32_t raster_group);

@@ -266,7 +266,17 @@ int dd_plan_set_kernel(dd_plan *plan, int32_t kernel)
     if (kernel == 1) { plan->kernel = 1; plan->kernel_req = 1; return DD_OK; }
     if (kernel == 2) {
         if (!plan->fast) return set_error(DD_ERR_ARG, "kernel 2 is not available for this plan");
+        if (fast_kernel_id(plan) != 2) {
+            int rc = fast_set_tile(plan, 0, 8);
+            if (rc) return rc;
+        }
         plan->kernel = 2; plan->kernel_req = 2; return DD_OK;
+    }
+    if (kernel == 3) {
+        if (!plan->fast) return set_error(DD_ERR_ARG, "kernel 3 is not available for this plan");
+        int rc = fast_set_tile(plan, 3, 8);
+        if (rc) return rc;
+        plan->kernel = 2; plan->kernel_req = 3; return DD_OK;
     }
     return set_error(DD_ERR_ARG, "unknown kernel %d", kernel);
 }
@@ -274,7 +284,7 @@ int dd_plan_set_kernel(dd_plan *plan, int32_t kernel)
 int dd_plan_get_kernel(const dd_plan *plan, int32_t *kernel)
 {
     if (!plan || !kernel) return set_error(DD_ERR_ARG, "NULL argument");
-    *kernel = plan->kernel;
+    *kernel = plan->kernel == 2 ? fast_kernel_id(plan) : plan->kernel;
     return DD_OK;
 }
 

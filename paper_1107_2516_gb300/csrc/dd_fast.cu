@@ -2,6 +2,7 @@
 // launch, and the autotuner that picks (configuration, raster group) by
 // timing them on the caller's data.
 #include "dd_fast_impl.cuh"
+#include "dd_lane_impl.cuh"
 
 #include <algorithm>
 #include <climits>
@@ -26,8 +27,22 @@ struct FastCfgData {
     double last_ms = -1.0;       // autotuner timing
 };
 
+struct LaneCfgData {
+    bool ok = false;
+    int ti = 0, dr = 0, nw = 0;
+    int nblk = 0, rs = 0, ch = 0, bar_off = 0;
+    size_t smem = 0;
+    int32_t *d_offs = nullptr;   // [nblk][nchans][nw*dr] offsets within the staged row
+    int32_t *d_base = nullptr;   // [nblk][nchans] row start relative to the tile start
+};
+
+// Tile configurations: indices [0, kNumFastCfg) are kernel 2 shapes,
+// [kNumFastCfg, kNumFastCfg + kNumLaneCfg) kernel 3 shapes.
+constexpr int kNumAllCfg = kNumFastCfg + kNumLaneCfg;
+
 struct FastPlan {
     FastCfgData cfg[kNumFastCfg];
+    LaneCfgData lane[kNumLaneCfg];
     int active = -1;
     int dgroup = 8;
     int al = 4;                  // row alignment in elements (16 bytes)
@@ -52,6 +67,66 @@ static cudaError_t prepare_cfg(int k, size_t optin)
     case 1: return fast_prepare_t20w12(optin);
     default: return fast_prepare_t28w8(optin);
     }
+}
+
+static cudaError_t launch_lane(int k, dd_dtype t, const LaneLaunch &a, cudaStream_t s)
+{
+    return k == 0 ? lane_launch_t16d4w8(t, a, s) : lane_launch_t16d8w8(t, a, s);
+}
+
+static cudaError_t prepare_lane(int k, size_t optin)
+{
+    return k == 0 ? lane_prepare_t16d4w8(optin) : lane_prepare_t16d8w8(optin);
+}
+
+static void free_lane(LaneCfgData &c)
+{
+    if (c.d_offs) cudaFree(c.d_offs);
+    if (c.d_base) cudaFree(c.d_base);
+    c.d_offs = nullptr; c.d_base = nullptr;
+    c.ok = false;
+}
+
+// Kernel 3 tables: per (DM block, channel) the aligned row start and every
+// DM trial's offset in the row.  c.ok stays false if rows do not fit.
+static int build_lane(const dd_plan *p, int ti, int dr, int nw, LaneCfgData &c)
+{
+    c = LaneCfgData();
+    c.ti = ti; c.dr = dr; c.nw = nw;
+    const int C = p->nchans, D = p->ndm, DB = dr * nw;
+    const int nblk = (D + DB - 1) / DB;
+    const int AL = elem_align(p->dtype);
+    std::vector<int32_t> offs((size_t)nblk * C * DB), base((size_t)nblk * C);
+    long long need = 0;
+    for (int b = 0; b < nblk; ++b)
+        for (int ch = 0; ch < C; ++ch) {
+            int lo = INT_MAX, hi = 0;
+            for (int j = 0; j < DB; ++j) {
+                const int d = p->delays[(size_t)std::min(b * DB + j, D - 1) * C + ch];
+                lo = std::min(lo, d); hi = std::max(hi, d);
+            }
+            const int row0 = lo - (lo % AL);
+            base[(size_t)b * C + ch] = row0;
+            for (int j = 0; j < DB; ++j)
+                offs[((size_t)b * C + ch) * DB + j] = p->delays[(size_t)std::min(b * DB + j, D - 1) * C + ch] - row0;
+            need = std::max<long long>(need, (long long)(hi - row0) + 32LL * ti);
+        }
+    const int rs = (int)((need + 15) / 16 * 16);
+    const size_t eb = in_elem_bytes(p->dtype);
+    const size_t budget = std::min<size_t>(p->smem_optin, 227 * 1024) - 1024;
+    const size_t per_ch = (size_t)rs * eb + DB * sizeof(int32_t);
+    const int ch = (int)std::min<size_t>(16, budget / (kStages * per_ch));
+    if (ch < 1) return DD_OK;
+    c.bar_off = (int)(((size_t)kStages * ch * per_ch + 15) / 16 * 16);
+    c.smem = (size_t)c.bar_off + kStages * sizeof(uint64_t);
+    c.nblk = nblk; c.rs = rs; c.ch = ch;
+    cudaError_t e = cudaMalloc(&c.d_offs, offs.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_base, base.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_offs, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { free_lane(c); return cuda_fail(e, "kernel 3 tables"); }
+    c.ok = true;
+    return DD_OK;
 }
 
 static void free_cfg(FastCfgData &c)
@@ -161,6 +236,12 @@ static TuneKey tune_key(const dd_plan *p)
     return TuneKey(p->nchans, p->ndm, (int)p->dtype, p->nsamp_in, p->fch1, p->foff, p->tsamp, d0, d1);
 }
 
+static bool cfg_ok(const FastPlan *f, int k)
+{
+    if (k < 0 || k >= kNumAllCfg) return false;
+    return k < kNumFastCfg ? f->cfg[k].ok : f->lane[k - kNumFastCfg].ok;
+}
+
 int fast_configure(dd_plan *p)
 {
     p->fast = nullptr;
@@ -169,9 +250,13 @@ int fast_configure(dd_plan *p)
     int rc = DD_OK;
     for (int k = 0; k < kNumFastCfg && rc == DD_OK; ++k)
         rc = build_cfg(p, kFastCfg[k].tr, kFastCfg[k].nw, f->cfg[k]);
+    for (int k = 0; k < kNumLaneCfg && rc == DD_OK; ++k)
+        rc = build_lane(p, kLaneCfg[k].ti, kLaneCfg[k].dr, kLaneCfg[k].nw, f->lane[k]);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < kNumFastCfg && rc == DD_OK && e == cudaSuccess; ++k)
         if (f->cfg[k].ok) e = prepare_cfg(k, p->smem_optin);
+    for (int k = 0; k < kNumLaneCfg && rc == DD_OK && e == cudaSuccess; ++k)
+        if (f->lane[k].ok) e = prepare_lane(k, p->smem_optin);
     if (rc == DD_OK && e == cudaSuccess) e = cudaMalloc(&f->d_err, sizeof(int));
     if (rc == DD_OK && e == cudaSuccess) e = cudaMemset(f->d_err, 0, sizeof(int));
     p->fast = f;
@@ -182,7 +267,7 @@ int fast_configure(dd_plan *p)
     if (f->active < 0) { fast_release(p); return DD_OK; }   // kernel 2 unavailable
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune_cache.find(tune_key(p));
-    if (it != g_tune_cache.end() && f->cfg[it->second.first].ok) {
+    if (it != g_tune_cache.end() && cfg_ok(f, it->second.first)) {
         f->active = it->second.first;
         f->dgroup = it->second.second;
     }
@@ -204,8 +289,34 @@ int fast_error(dd_plan *p, cudaStream_t s)
     return DD_OK;
 }
 
+static int lane_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s)
+{
+    FastPlan *f = static_cast<FastPlan *>(p->fast);
+    LaneCfgData &c = f->lane[k];
+    const int tile = 32 * c.ti;
+    const int64_t ntile = (p->nsamp_out + tile - 1) / tile;
+    if (ntile * c.nblk > INT32_MAX) return generic_execute(p, in, pitch, out, s);
+    const int64_t np = ntile * c.nblk;
+    int rc = ensure_partials_public(p, np);
+    if (rc) return rc;
+    LaneLaunch a;
+    a.in = in; a.pitch = pitch;
+    a.nsamp_in_al = (p->nsamp_in + f->al - 1) / f->al * f->al;
+    a.nchans = p->nchans; a.ndm = p->ndm; a.nout = p->nsamp_out;
+    a.offs = c.d_offs; a.base = c.d_base;
+    a.rs = c.rs; a.ch = c.ch; a.bar_off = c.bar_off; a.nblk = c.nblk;
+    a.ntile = ntile; a.dgroup = std::max(1, std::min(dgroup, c.nblk));
+    a.out = out; a.partials = p->d_partials; a.err = f->d_err; a.smem = c.smem;
+    cudaError_t e = launch_lane(k, p->dtype, a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launch lane_kernel");
+    p->n_partials = np;
+    p->stats_out = out;
+    return DD_OK;
+}
+
 static int fast_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s)
 {
+    if (k >= kNumFastCfg) return lane_run(p, k - kNumFastCfg, dgroup, in, pitch, out, s);
     FastPlan *f = static_cast<FastPlan *>(p->fast);
     FastCfgData &c = f->cfg[k];
     const int tile = 32 * c.tr;
@@ -249,8 +360,8 @@ int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStre
     float best = 1e30f;
     int bk = f->active, bg = f->dgroup, rc = DD_OK;
     const int groups[] = {4, 8, 16};
-    for (int k = 0; k < kNumFastCfg && rc == DD_OK; ++k) {
-        if (!f->cfg[k].ok) continue;
+    for (int k = 0; k < kNumAllCfg && rc == DD_OK; ++k) {
+        if (!cfg_ok(f, k)) continue;
         rc = fast_run(p, k, 8, in, pitch, out, s);             // warm-up (caches, clocks)
         for (int gi = 0; gi < 3 && rc == DD_OK; ++gi) {
             cudaEventRecord(e0, s);
@@ -260,7 +371,7 @@ int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStre
             if (cudaEventSynchronize(e1) != cudaSuccess) { rc = set_error(DD_ERR_CUDA, "autotune sync"); break; }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            f->cfg[k].last_ms = ms;
+            if (k < kNumFastCfg) f->cfg[k].last_ms = ms;
             if (ms < best) { best = ms; bk = k; bg = groups[gi]; }
         }
     }
@@ -280,7 +391,7 @@ int fast_set_tile(dd_plan *p, int cfg, int dgroup)
 {
     FastPlan *f = static_cast<FastPlan *>(p->fast);
     if (!f) return set_error(DD_ERR_ARG, "kernel 2 unavailable for this plan");
-    if (cfg < 0 || cfg >= kNumFastCfg || !f->cfg[cfg].ok)
+    if (!cfg_ok(f, cfg))
         return set_error(DD_ERR_ARG, "tile configuration %d not available for this plan", cfg);
     if (dgroup < 1) return set_error(DD_ERR_ARG, "raster group must be >= 1");
     f->active = cfg;
@@ -294,9 +405,20 @@ int fast_get_tile(const dd_plan *p, int *cfg, int *dgroup, int *tr, int *nw)
     if (!f) return set_error(DD_ERR_ARG, "kernel 2 unavailable for this plan");
     if (cfg) *cfg = f->active;
     if (dgroup) *dgroup = f->dgroup;
-    if (tr) *tr = f->cfg[f->active].tr;
-    if (nw) *nw = f->cfg[f->active].nw;
+    if (f->active < kNumFastCfg) {
+        if (tr) *tr = f->cfg[f->active].tr;
+        if (nw) *nw = f->cfg[f->active].nw;
+    } else {
+        if (tr) *tr = f->lane[f->active - kNumFastCfg].ti;
+        if (nw) *nw = f->lane[f->active - kNumFastCfg].nw;
+    }
     return DD_OK;
+}
+
+int fast_kernel_id(const dd_plan *p)
+{
+    const FastPlan *f = static_cast<const FastPlan *>(p->fast);
+    return (f && f->active >= kNumFastCfg) ? 3 : 2;
 }
 
 void fast_release(dd_plan *p)
@@ -304,6 +426,7 @@ void fast_release(dd_plan *p)
     FastPlan *f = static_cast<FastPlan *>(p->fast);
     if (!f) return;
     for (int k = 0; k < kNumFastCfg; ++k) free_cfg(f->cfg[k]);
+    for (int k = 0; k < kNumLaneCfg; ++k) free_lane(f->lane[k]);
     if (f->d_err) cudaFree(f->d_err);
     delete f;
     p->fast = nullptr;

@@ -112,5 +112,6 @@ int fast_error(dd_plan *p, cudaStream_t s);
 int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStream_t s);
 int fast_set_tile(dd_plan *p, int cfg, int dgroup);
 int fast_get_tile(const dd_plan *p, int *cfg, int *dgroup, int *tr, int *nw);
+int fast_kernel_id(const dd_plan *p);
 
 }  // namespace dd

@@ -1,0 +1,212 @@
+// Kernel 3: lane-interleaved brute-force de-dispersion (Section 3.1),
+//   out[dm][t] = sum_c in[c][t + d(c,dm)].
+//
+// Block = NW warps sharing one time tile of 32*TI samples; lane l owns
+// samples t0 + l + 32*i (i < TI) and each warp owns DR DM trials, so a thread
+// accumulates DR x TI outputs.  Per channel the block stages (one TMA bulk
+// copy) the input span of all its DM trials; for each DM trial a warp adds
+// row[o + l + 32 i] with o the trial's warp-uniform offset: 32 consecutive
+// words per load, conflict-free at any alignment, no branches.  Every add
+// costs one shared-memory word, so the kernel is bounded by shared-memory
+// bandwidth (32 words/clk/SM = 1/4 of the FP32 add rate); it trades kernel
+// 2's register reuse for straight-line code and high occupancy.
+#pragma once
+
+#include "dd_fast_impl.cuh"
+
+namespace dd {
+
+struct LaneLaunch {
+    const void *in;
+    int64_t pitch, nsamp_in_al;
+    int nchans, ndm;
+    int64_t nout;
+    const int32_t *offs;   // [nblk][nchans][NW*DR] element offsets within the staged row
+    const int32_t *base;   // [nblk][nchans] row start relative to the tile start (aligned)
+    int rs, ch, bar_off, nblk;
+    int64_t ntile;
+    int dgroup;
+    void *out, *partials;
+    int *err;
+    size_t smem;
+};
+
+template <typename Tin> __device__ __forceinline__ float lane_ld(const Tin *p);
+template <> __device__ __forceinline__ float lane_ld<float>(const float *p) { return *p; }
+template <> __device__ __forceinline__ float lane_ld<__half>(const __half *p) { return __half2float(*p); }
+template <> __device__ __forceinline__ float lane_ld<uint8_t>(const uint8_t *p) { return (float)*p; }
+
+template <typename Tin, bool kInt, int TI, int DR, int NW>
+__global__ void __launch_bounds__(NW * 32) lane_kernel(LaneLaunch a)
+{
+    constexpr int kTile = 32 * TI, kDmBlk = DR * NW;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const Tin *__restrict__ in = static_cast<const Tin *>(a.in);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nchans = a.nchans, rs = a.rs, ch = a.ch;
+
+    // raster (as kernel 2): DM blocks in groups, time tiles slowest within a group
+    const int64_t lin = blockIdx.x;
+    const int64_t per_group = (int64_t)a.dgroup * a.ntile;
+    const int64_t grp = lin / per_group;
+    const int64_t rr = lin - grp * per_group;
+    const int gsize = min(a.dgroup, a.nblk - (int)grp * a.dgroup);
+    const int blk = (int)grp * a.dgroup + (int)(rr % gsize);
+    const int64_t t0 = (rr / gsize) * kTile;
+    const int dm0 = blk * kDmBlk;
+
+    // layout: [kStages][ch][rs] Tin rows | [kStages][ch][kDmBlk] int32 offsets | mbar at bar_off
+    const size_t stage_elems = (size_t)ch * rs;
+    Tin *rows = reinterpret_cast<Tin *>(smem);
+    int32_t *soffs = reinterpret_cast<int32_t *>(smem + kStages * stage_elems * sizeof(Tin));
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.bar_off);
+    const int32_t *boffs = a.offs + (size_t)blk * nchans * kDmBlk;
+    const int32_t *bbase = a.base + (size_t)blk * nchans;
+    const int nst = (nchans + ch - 1) / ch;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    auto row_bytes = [&](int c, int64_t &g) -> uint32_t {
+        g = t0 + bbase[c];
+        int64_t n = a.nsamp_in_al - g;
+        n = n < 0 ? 0 : (n > rs ? rs : n);
+        return (uint32_t)(n * (int64_t)sizeof(Tin));
+    };
+    auto issue = [&](int s) {
+        const int buf = s % kStages;
+        const int c0 = s * ch;
+        const int cn = min(ch, nchans - c0);
+        uint32_t bytes = (uint32_t)(cn * kDmBlk * sizeof(int32_t));
+        for (int cc = 0; cc < cn; ++cc) { int64_t g; bytes += row_bytes(c0 + cc, g); }
+        mbar_arrive_tx(&bar[buf], bytes);
+        bulk_g2s(soffs + (size_t)buf * ch * kDmBlk, boffs + (size_t)c0 * kDmBlk,
+                 (uint32_t)(cn * kDmBlk * sizeof(int32_t)), &bar[buf]);
+        for (int cc = 0; cc < cn; ++cc) {
+            int64_t g;
+            const uint32_t nb = row_bytes(c0 + cc, g);
+            if (nb)
+                bulk_g2s(rows + (size_t)buf * stage_elems + (size_t)cc * rs,
+                         in + (size_t)(c0 + cc) * a.pitch + g, nb, &bar[buf]);
+        }
+    };
+
+    float acc[DR][TI];
+#pragma unroll
+    for (int j = 0; j < DR; ++j)
+#pragma unroll
+        for (int i = 0; i < TI; ++i) acc[j][i] = 0.f;
+
+    if (tid == 0)
+        for (int s = 0; s < kStages - 1 && s < nst; ++s) issue(s);
+
+    bool ok = true;
+    for (int s = 0; s < nst; ++s) {
+        if (tid == 0 && s + kStages - 1 < nst) issue(s + kStages - 1);
+        const int buf = s % kStages;
+        if (!mbar_wait(&bar[buf], (uint32_t)((s / kStages) & 1), a.err)) { ok = false; break; }
+        const int cn = min(ch, nchans - s * ch);
+        const Tin *srow = rows + (size_t)buf * stage_elems + lane;
+        const int32_t *so = soffs + (size_t)buf * ch * kDmBlk + warp * DR;
+        for (int cc = 0; cc < cn; ++cc) {
+            const Tin *r = srow + (size_t)cc * rs;
+            int o[DR];
+#pragma unroll
+            for (int j = 0; j < DR; ++j) o[j] = so[cc * kDmBlk + j];
+#pragma unroll
+            for (int j = 0; j < DR; ++j) {
+                const Tin *p = r + o[j];
+#pragma unroll
+                for (int i = 0; i < TI; ++i) acc[j][i] += lane_ld<Tin>(p + 32 * i);
+            }
+        }
+        __syncthreads();
+    }
+    if (!ok) return;
+
+    // epilogue: lanes hold consecutive samples, so stores are coalesced directly
+    const int64_t nout = a.nout;
+    if constexpr (kInt) {
+        long long n = 0, s = 0;
+        unsigned long long q = 0;
+        int32_t *out = reinterpret_cast<int32_t *>(a.out);
+#pragma unroll
+        for (int j = 0; j < DR; ++j) {
+            const int dm = dm0 + warp * DR + j;
+#pragma unroll
+            for (int i = 0; i < TI; ++i) {
+                const int64_t t = t0 + lane + 32 * i;
+                if (dm < a.ndm && t < nout) {
+                    const long long v = __float2int_rn(acc[j][i]);
+                    out[(size_t)dm * nout + t] = (int32_t)v;
+                    n++; s += v; q += (unsigned long long)(v * v);
+                }
+            }
+        }
+        block_stat_i(n, s, q, reinterpret_cast<StatI *>(a.partials) + lin);
+    } else {
+        int n = 0;
+        float s = 0.f;
+        float *out = reinterpret_cast<float *>(a.out);
+#pragma unroll
+        for (int j = 0; j < DR; ++j) {
+            const int dm = dm0 + warp * DR + j;
+#pragma unroll
+            for (int i = 0; i < TI; ++i) {
+                const int64_t t = t0 + lane + 32 * i;
+                if (dm < a.ndm && t < nout) {
+                    out[(size_t)dm * nout + t] = acc[j][i];
+                    n++; s += acc[j][i];
+                }
+            }
+        }
+        const float m = n ? s / (float)n : 0.f;
+        float q = 0.f;
+#pragma unroll
+        for (int j = 0; j < DR; ++j) {
+            const int dm = dm0 + warp * DR + j;
+#pragma unroll
+            for (int i = 0; i < TI; ++i) {
+                const int64_t t = t0 + lane + 32 * i;
+                if (dm < a.ndm && t < nout) { const float d = acc[j][i] - m; q += d * d; }
+            }
+        }
+        block_stat_f32(n, s, q, reinterpret_cast<StatF *>(a.partials) + lin);
+    }
+}
+
+template <int TI, int DR, int NW>
+cudaError_t lane_launch_cfg(dd_dtype t, const LaneLaunch &a, cudaStream_t s)
+{
+    const unsigned grid = (unsigned)(a.ntile * a.nblk);
+    switch (t) {
+    case DD_F32: lane_kernel<float, false, TI, DR, NW><<<grid, NW * 32, a.smem, s>>>(a); break;
+    case DD_F16: lane_kernel<__half, false, TI, DR, NW><<<grid, NW * 32, a.smem, s>>>(a); break;
+    case DD_U8: lane_kernel<uint8_t, true, TI, DR, NW><<<grid, NW * 32, a.smem, s>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+template <int TI, int DR, int NW>
+cudaError_t lane_prepare_cfg(size_t optin)
+{
+    cudaError_t e = allow_max_dynamic_smem((const void *)lane_kernel<float, false, TI, DR, NW>, optin);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem((const void *)lane_kernel<__half, false, TI, DR, NW>, optin);
+    if (e == cudaSuccess) e = allow_max_dynamic_smem((const void *)lane_kernel<uint8_t, true, TI, DR, NW>, optin);
+    return e;
+}
+
+// Configurations compiled into the library: {samples per lane, DM trials per warp, warps}.
+struct LaneShape { int ti, dr, nw; };
+constexpr int kNumLaneCfg = 2;
+constexpr LaneShape kLaneCfg[kNumLaneCfg] = {{16, 4, 8}, {16, 8, 8}};
+
+cudaError_t lane_launch_t16d4w8(dd_dtype t, const LaneLaunch &a, cudaStream_t s);
+cudaError_t lane_launch_t16d8w8(dd_dtype t, const LaneLaunch &a, cudaStream_t s);
+cudaError_t lane_prepare_t16d4w8(size_t optin);
+cudaError_t lane_prepare_t16d8w8(size_t optin);
+
+}  // namespace dd
