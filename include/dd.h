@@ -178,8 +178,9 @@ DD_API int dd_plan_autotune(dd_plan *plan, const void *in_dev, int64_t in_pitch,
 
 /* Choose kernel 2's tile configuration explicitly.  config indexes the
  * compiled list {kernel 2 — 0: 36 samples x 4 DM trials per thread, 8 warps;
- * 1: 20 x 4, 12 warps; 2: 28 x 4, 8 warps; kernel 3 — 3: 16 samples per
- * lane x 4 DM trials per warp, 8 warps; 4: 16 x 8, 8 warps}; raster_group (>= 1) is the
+ * 1: 20 x 4, 12 warps; 2: 28 x 4, 8 warps; kernel 3 (samples per lane x
+ * DM trials per warp, warps) — 3: 16 x 4, 8 warps; 4: 16 x 8, 8 warps;
+ * 5: 16 x 8, 4 warps; 6: 8 x 16, 4 warps}; raster_group (>= 1) is the
  * number of DM blocks whose time tiles are swept together.  DD_ERR_ARG if
  * the configuration cannot run this plan. */
 DD_API int dd_plan_set_tile(dd_plan *plan, int32_t config, int32_t raster_group);

@@ -71,12 +71,22 @@ static cudaError_t prepare_cfg(int k, size_t optin)
 
 static cudaError_t launch_lane(int k, dd_dtype t, const LaneLaunch &a, cudaStream_t s)
 {
-    return k == 0 ? lane_launch_t16d4w8(t, a, s) : lane_launch_t16d8w8(t, a, s);
+    switch (k) {
+    case 0: return lane_launch_c0(t, a, s);
+    case 1: return lane_launch_c1(t, a, s);
+    case 2: return lane_launch_c2(t, a, s);
+    default: return lane_launch_c3(t, a, s);
+    }
 }
 
 static cudaError_t prepare_lane(int k, size_t optin)
 {
-    return k == 0 ? lane_prepare_t16d4w8(optin) : lane_prepare_t16d8w8(optin);
+    switch (k) {
+    case 0: return lane_prepare_c0(optin);
+    case 1: return lane_prepare_c1(optin);
+    case 2: return lane_prepare_c2(optin);
+    default: return lane_prepare_c3(optin);
+    }
 }
 
 static void free_lane(LaneCfgData &c)
@@ -89,7 +99,7 @@ static void free_lane(LaneCfgData &c)
 
 // Kernel 3 tables: per (DM block, channel) the aligned row start and every
 // DM trial's offset in the row.  c.ok stays false if rows do not fit.
-static int build_lane(const dd_plan *p, int ti, int dr, int nw, LaneCfgData &c)
+static int build_lane(const dd_plan *p, int ti, int dr, int nw, int minb, LaneCfgData &c)
 {
     c = LaneCfgData();
     c.ti = ti; c.dr = dr; c.nw = nw;
@@ -113,7 +123,8 @@ static int build_lane(const dd_plan *p, int ti, int dr, int nw, LaneCfgData &c)
         }
     const int rs = (int)((need + 15) / 16 * 16);
     const size_t eb = in_elem_bytes(p->dtype);
-    const size_t budget = std::min<size_t>(p->smem_optin, 227 * 1024) - 1024;
+    // shared memory of one block: the SM's 228 KB split between `minb` resident blocks
+    const size_t budget = std::min<size_t>(p->smem_optin, (228 * 1024) / (size_t)minb - 1024) - 1024;
     const size_t per_ch = (size_t)rs * eb + DB * sizeof(int32_t);
     const int ch = (int)std::min<size_t>(16, budget / (kStages * per_ch));
     if (ch < 1) return DD_OK;
@@ -251,7 +262,7 @@ int fast_configure(dd_plan *p)
     for (int k = 0; k < kNumFastCfg && rc == DD_OK; ++k)
         rc = build_cfg(p, kFastCfg[k].tr, kFastCfg[k].nw, f->cfg[k]);
     for (int k = 0; k < kNumLaneCfg && rc == DD_OK; ++k)
-        rc = build_lane(p, kLaneCfg[k].ti, kLaneCfg[k].dr, kLaneCfg[k].nw, f->lane[k]);
+        rc = build_lane(p, kLaneCfg[k].ti, kLaneCfg[k].dr, kLaneCfg[k].nw, kLaneCfg[k].minb, f->lane[k]);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < kNumFastCfg && rc == DD_OK && e == cudaSuccess; ++k)
         if (f->cfg[k].ok) e = prepare_cfg(k, p->smem_optin);

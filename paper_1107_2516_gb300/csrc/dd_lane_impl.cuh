@@ -36,8 +36,8 @@ template <> __device__ __forceinline__ float lane_ld<float>(const float *p) { re
 template <> __device__ __forceinline__ float lane_ld<__half>(const __half *p) { return __half2float(*p); }
 template <> __device__ __forceinline__ float lane_ld<uint8_t>(const uint8_t *p) { return (float)*p; }
 
-template <typename Tin, bool kInt, int TI, int DR, int NW>
-__global__ void __launch_bounds__(NW * 32) lane_kernel(LaneLaunch a)
+template <typename Tin, bool kInt, int TI, int DR, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) lane_kernel(LaneLaunch a)
 {
     constexpr int kTile = 32 * TI, kDmBlk = DR * NW;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -178,35 +178,42 @@ __global__ void __launch_bounds__(NW * 32) lane_kernel(LaneLaunch a)
     }
 }
 
-template <int TI, int DR, int NW>
+template <int TI, int DR, int NW, int MINB>
 cudaError_t lane_launch_cfg(dd_dtype t, const LaneLaunch &a, cudaStream_t s)
 {
     const unsigned grid = (unsigned)(a.ntile * a.nblk);
     switch (t) {
-    case DD_F32: lane_kernel<float, false, TI, DR, NW><<<grid, NW * 32, a.smem, s>>>(a); break;
-    case DD_F16: lane_kernel<__half, false, TI, DR, NW><<<grid, NW * 32, a.smem, s>>>(a); break;
-    case DD_U8: lane_kernel<uint8_t, true, TI, DR, NW><<<grid, NW * 32, a.smem, s>>>(a); break;
+    case DD_F32: lane_kernel<float, false, TI, DR, NW, MINB><<<grid, NW * 32, a.smem, s>>>(a); break;
+    case DD_F16: lane_kernel<__half, false, TI, DR, NW, MINB><<<grid, NW * 32, a.smem, s>>>(a); break;
+    case DD_U8: lane_kernel<uint8_t, true, TI, DR, NW, MINB><<<grid, NW * 32, a.smem, s>>>(a); break;
     }
     return cudaGetLastError();
 }
 
-template <int TI, int DR, int NW>
+template <int TI, int DR, int NW, int MINB>
 cudaError_t lane_prepare_cfg(size_t optin)
 {
-    cudaError_t e = allow_max_dynamic_smem((const void *)lane_kernel<float, false, TI, DR, NW>, optin);
-    if (e == cudaSuccess) e = allow_max_dynamic_smem((const void *)lane_kernel<__half, false, TI, DR, NW>, optin);
-    if (e == cudaSuccess) e = allow_max_dynamic_smem((const void *)lane_kernel<uint8_t, true, TI, DR, NW>, optin);
+    cudaError_t e = allow_max_dynamic_smem((const void *)lane_kernel<float, false, TI, DR, NW, MINB>, optin);
+    if (e == cudaSuccess)
+        e = allow_max_dynamic_smem((const void *)lane_kernel<__half, false, TI, DR, NW, MINB>, optin);
+    if (e == cudaSuccess)
+        e = allow_max_dynamic_smem((const void *)lane_kernel<uint8_t, true, TI, DR, NW, MINB>, optin);
     return e;
 }
 
-// Configurations compiled into the library: {samples per lane, DM trials per warp, warps}.
-struct LaneShape { int ti, dr, nw; };
-constexpr int kNumLaneCfg = 2;
-constexpr LaneShape kLaneCfg[kNumLaneCfg] = {{16, 4, 8}, {16, 8, 8}};
+// Configurations compiled into the library: {samples per lane, DM trials per
+// warp, warps per block, resident blocks per SM the register budget targets}.
+struct LaneShape { int ti, dr, nw, minb; };
+constexpr int kNumLaneCfg = 4;
+constexpr LaneShape kLaneCfg[kNumLaneCfg] = {{16, 4, 8, 2}, {16, 8, 8, 1}, {16, 8, 4, 3}, {8, 16, 4, 3}};
 
-cudaError_t lane_launch_t16d4w8(dd_dtype t, const LaneLaunch &a, cudaStream_t s);
-cudaError_t lane_launch_t16d8w8(dd_dtype t, const LaneLaunch &a, cudaStream_t s);
-cudaError_t lane_prepare_t16d4w8(size_t optin);
-cudaError_t lane_prepare_t16d8w8(size_t optin);
+cudaError_t lane_launch_c0(dd_dtype t, const LaneLaunch &a, cudaStream_t s);
+cudaError_t lane_launch_c1(dd_dtype t, const LaneLaunch &a, cudaStream_t s);
+cudaError_t lane_launch_c2(dd_dtype t, const LaneLaunch &a, cudaStream_t s);
+cudaError_t lane_launch_c3(dd_dtype t, const LaneLaunch &a, cudaStream_t s);
+cudaError_t lane_prepare_c0(size_t optin);
+cudaError_t lane_prepare_c1(size_t optin);
+cudaError_t lane_prepare_c2(size_t optin);
+cudaError_t lane_prepare_c3(size_t optin);
 
 }  // namespace dd

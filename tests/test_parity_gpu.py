@@ -102,7 +102,8 @@ def test_small_workload_parity(dtype, kernel):
     assert (int(best["dm_idx"]), int(best["t"]), int(best["width_idx"])) == (30, 4000, 2)
 
 
-@pytest.mark.parametrize("tile", [(0, 1), (0, 3), (1, 8), (1, 2), (2, 16), (3, 8), (3, 1), (4, 4)])
+@pytest.mark.parametrize("tile", [(0, 1), (0, 3), (1, 8), (1, 2), (2, 16), (3, 8), (3, 1), (4, 4),
+                                  (5, 8), (5, 3), (6, 16), (6, 2)])
 @pytest.mark.parametrize("dtype", ["f32", "u8", "f16"])
 def test_small_workload_tile_configs(dtype, tile):
     # every compiled tile configuration of kernels 2 and 3 and several raster
@@ -123,7 +124,7 @@ def test_autotune_keeps_parity():
     out = torch.empty(wl.ndm * plan.nsamp_out, dtype=torch.float32, device="cuda")
     plan.autotune(x, wl.nsamp, out)
     cfg, group, tr, nw = plan.tile
-    assert 0 <= cfg < 5 and group in (4, 8, 16) and tr in (16, 20, 28, 36) and nw in (8, 12)
+    assert 0 <= cfg < 7 and group in (4, 8, 16) and tr in (8, 16, 20, 28, 36) and nw in (4, 8, 12)
     plan.execute(x, wl.nsamp, out)
     torch.cuda.synchronize()
     d_o, m_o = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
