@@ -158,21 +158,25 @@ DD_API int dd_process_host(dd_plan *plan, const void *in_host, int64_t in_pitch,
 /* Select the de-dispersion kernel for a plan: 0 = automatic (default),
  * 1 = generic shared-memory kernel, 2 = register-blocked kernel (window
  * reused across 4 DM trials per thread), 3 = lane-interleaved kernel (one
- * conflict-free shared load per add, no branches).  Kernels 2 and 3 share the
+ * conflict-free shared load per add, no branches), 4 = tensor-memory window
+ * kernel (each staged input word copied once into TMEM and read back by every
+ * DM trial of the warp at a runtime column offset).  Kernels 2-4 share the
  * tile-configuration list of dd_plan_set_tile.  Returns DD_ERR_ARG if the
  * requested kernel cannot run this plan. */
 DD_API int dd_plan_set_kernel(dd_plan *plan, int32_t kernel);
 
-/* Kernel that dd_execute will launch for this plan (1, 2 or 3, see above). */
+/* Kernel that dd_execute will launch for this plan (1 to 4, see above). */
 DD_API int dd_plan_get_kernel(const dd_plan *plan, int32_t *kernel);
 
-/* Autotuner for the register-blocked kernel (kernel 2): runs the plan on the
- * caller's buffers once per compiled tile configuration and raster group
- * (see dd_plan_set_tile), times each with CUDA events on `stream`, keeps the
- * fastest for this plan and caches the choice process-wide for plans of the
- * same shape.  Writes out_dev (several full executions); synchronises
- * `stream`.  A no-op (DD_OK) when kernel 2 cannot run the plan or the input
- * rows are not 16-byte aligned. */
+/* Autotuner for the tiled kernels: runs the plan on the caller's buffers
+ * once per compiled tile configuration of kernels 2 and 3 (0-6, see
+ * dd_plan_set_tile) and raster group, times each with CUDA events on
+ * `stream`, keeps the fastest for this plan and caches the choice
+ * process-wide for plans of the same shape.  Kernel 4 is not timed (slower on
+ * every plan measured); dd_plan_set_kernel(plan, 4) selects it.  Writes
+ * out_dev (several full executions); synchronises `stream`.  A no-op (DD_OK)
+ * when the tiled kernels cannot run the plan or the input rows are not
+ * 16-byte aligned. */
 DD_API int dd_plan_autotune(dd_plan *plan, const void *in_dev, int64_t in_pitch, void *out_dev,
                             void *stream);
 
@@ -180,14 +184,16 @@ DD_API int dd_plan_autotune(dd_plan *plan, const void *in_dev, int64_t in_pitch,
  * compiled list {kernel 2 — 0: 36 samples x 4 DM trials per thread, 8 warps;
  * 1: 20 x 4, 12 warps; 2: 28 x 4, 8 warps; kernel 3 (samples per lane x
  * DM trials per warp, warps) — 3: 16 x 4, 8 warps; 4: 16 x 8, 8 warps;
- * 5: 16 x 8, 4 warps; 6: 8 x 16, 4 warps}; raster_group (>= 1) is the
- * number of DM blocks whose time tiles are swept together.  DD_ERR_ARG if
- * the configuration cannot run this plan. */
+ * 5: 16 x 8, 4 warps; 6: 8 x 16, 4 warps; kernel 4 (samples per lane x DM
+ * trials per warp, warps) — 7: 20 x 4, 8 warps; 8: 12 x 8, 8 warps};
+ * raster_group (>= 1) is the number of DM blocks whose time tiles are swept
+ * together.  DD_ERR_ARG if the configuration cannot run this plan. */
 DD_API int dd_plan_set_tile(dd_plan *plan, int32_t config, int32_t raster_group);
 
-/* Current kernel-2 choice: configuration index, raster group, samples per
- * thread and warps per block (any pointer may be NULL).  DD_ERR_ARG if
- * kernel 2 cannot run this plan. */
+/* Current tiled-kernel choice: configuration index, raster group, samples
+ * per thread (kernel 2) or per lane (kernels 3, 4) and warps per block (any
+ * pointer may be NULL).  DD_ERR_ARG if the tiled kernels cannot run this
+ * plan. */
 DD_API int dd_plan_get_tile(const dd_plan *plan, int32_t *config, int32_t *raster_group,
                             int32_t *samples_per_thread, int32_t *warps_per_block);
 

@@ -278,6 +278,12 @@ int dd_plan_set_kernel(dd_plan *plan, int32_t kernel)
         if (rc) return rc;
         plan->kernel = 2; plan->kernel_req = 3; return DD_OK;
     }
+    if (kernel == 4) {
+        if (!plan->fast) return set_error(DD_ERR_ARG, "kernel 4 is not available for this plan");
+        int rc = fast_set_tile(plan, 7, 8);
+        if (rc) return rc;
+        plan->kernel = 2; plan->kernel_req = 4; return DD_OK;
+    }
     return set_error(DD_ERR_ARG, "unknown kernel %d", kernel);
 }
 

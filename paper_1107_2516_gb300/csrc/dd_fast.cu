@@ -3,6 +3,7 @@
 // timing them on the caller's data.
 #include "dd_fast_impl.cuh"
 #include "dd_lane_impl.cuh"
+#include "dd_tmem_impl.cuh"
 
 #include <algorithm>
 #include <climits>
@@ -36,13 +37,24 @@ struct LaneCfgData {
     int32_t *d_base = nullptr;   // [nblk][nchans] row start relative to the tile start
 };
 
+struct TmemCfgData {
+    bool ok = false;
+    int n = 0, dbw = 0, nw = 0;
+    int nblk = 0, rs = 0, ch = 0, bar_off = 0, dbp = 0, wmax = 0;
+    size_t smem = 0;
+    int32_t *d_tab = nullptr;    // [nblk][nchans][dbp] per-warp window records
+    int32_t *d_base = nullptr;   // [nblk][nchans] row start relative to the tile start
+};
+
 // Tile configurations: indices [0, kNumFastCfg) are kernel 2 shapes,
-// [kNumFastCfg, kNumFastCfg + kNumLaneCfg) kernel 3 shapes.
-constexpr int kNumAllCfg = kNumFastCfg + kNumLaneCfg;
+// [kNumFastCfg, kLaneEnd) kernel 3 shapes, [kLaneEnd, kNumAllCfg) kernel 4.
+constexpr int kLaneEnd = kNumFastCfg + kNumLaneCfg;
+constexpr int kNumAllCfg = kLaneEnd + kNumTmemCfg;
 
 struct FastPlan {
     FastCfgData cfg[kNumFastCfg];
     LaneCfgData lane[kNumLaneCfg];
+    TmemCfgData tm[kNumTmemCfg];
     int active = -1;
     int dgroup = 8;
     int al = 4;                  // row alignment in elements (16 bytes)
@@ -136,6 +148,87 @@ static int build_lane(const dd_plan *p, int ti, int dr, int nw, int minb, LaneCf
     if (e == cudaSuccess) e = cudaMemcpy(c.d_offs, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c.d_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { free_lane(c); return cuda_fail(e, "kernel 3 tables"); }
+    c.ok = true;
+    return DD_OK;
+}
+
+static cudaError_t launch_tmem(int k, dd_dtype t, const TmemLaunch &a, cudaStream_t s)
+{
+    return k == 0 ? tmem_launch_c0(t, a, s) : tmem_launch_c1(t, a, s);
+}
+
+static cudaError_t prepare_tmem(int k, size_t optin)
+{
+    return k == 0 ? tmem_prepare_c0(optin) : tmem_prepare_c1(optin);
+}
+
+static void free_tmem(TmemCfgData &c)
+{
+    if (c.d_tab) cudaFree(c.d_tab);
+    if (c.d_base) cudaFree(c.d_base);
+    c.d_tab = nullptr; c.d_base = nullptr;
+    c.ok = false;
+}
+
+// Kernel 4 tables.  Per (DM block, channel): the block's aligned row start
+// (base), and per warp {wbase, kc8, DBW column offsets}: the warp's window
+// starts wbase elements into the staged row (a multiple of 4), spans 8*kc8
+// columns, and trial j reads columns offs[j] .. offs[j]+N-1 of it.  c.ok
+// stays false if a window exceeds the warp's TMEM buffer or the rows do not
+// fit in shared memory.
+static int build_tmem(const dd_plan *p, int n, int dbw, int nw, TmemCfgData &c)
+{
+    c = TmemCfgData();
+    c.n = n; c.dbw = dbw; c.nw = nw;
+    const int C = p->nchans, D = p->ndm, DB = dbw * nw;
+    const int nblk = (D + DB - 1) / DB;
+    const int AL = elem_align(p->dtype);
+    const int rec = dbw + 2;
+    const int dbp = (nw * rec + 3) / 4 * 4;
+    const int kbuf = 512 / (nw / 4) / 2;           // TMEM columns of one window buffer
+    std::vector<int32_t> tab((size_t)nblk * C * dbp, 0), base((size_t)nblk * C);
+    auto dl = [&](int dm, int ch) { return p->delays[(size_t)std::min(dm, D - 1) * C + ch]; };
+    long long need = 0;
+    int wmax = 0;
+    for (int b = 0; b < nblk; ++b)
+        for (int ch = 0; ch < C; ++ch) {
+            int lo = INT_MAX;
+            for (int j = 0; j < DB; ++j) lo = std::min(lo, dl(b * DB + j, ch));
+            const int row0 = lo - (lo % AL);
+            base[(size_t)b * C + ch] = row0;
+            for (int w = 0; w < nw; ++w) {
+                int wlo = INT_MAX, whi = 0;
+                for (int j = 0; j < dbw; ++j) {
+                    const int d = dl(b * DB + w * dbw + j, ch) - row0;
+                    wlo = std::min(wlo, d); whi = std::max(whi, d);
+                }
+                const int wbase = wlo - (wlo % 4);
+                const int kc8 = (whi - wbase + n + 7) / 8;
+                int32_t *t = &tab[((size_t)b * C + ch) * dbp + (size_t)w * rec];
+                t[0] = wbase; t[1] = kc8;
+                for (int j = 0; j < dbw; ++j) t[2 + j] = dl(b * DB + w * dbw + j, ch) - row0 - wbase;
+                wmax = std::max(wmax, 8 * kc8);
+                need = std::max<long long>(need, (long long)wbase + 31LL * n + 8LL * kc8);
+            }
+        }
+    if (wmax > kbuf) return DD_OK;
+    const int rs = (int)((need + 15) / 16 * 16);
+    const size_t eb = in_elem_bytes(p->dtype);
+    const size_t budget = std::min<size_t>(p->smem_optin, 227 * 1024) - 1024 - 64;
+    const size_t per_ch = (size_t)rs * eb + (size_t)dbp * sizeof(int32_t);
+    const int ch = (int)std::min<size_t>(16, budget / (kStages * per_ch));
+    if (ch < 1) return DD_OK;
+    c.bar_off = (int)(((size_t)kStages * ch * per_ch + 15) / 16 * 16);
+    c.smem = (size_t)c.bar_off + kStages * sizeof(uint64_t) + 16;
+    // more than half of the SM's shared memory: one block (and one 512-column
+    // TMEM allocation) per SM
+    c.smem = std::max<size_t>(c.smem, std::min<size_t>(p->smem_optin, 120 * 1024));
+    c.nblk = nblk; c.rs = rs; c.ch = ch; c.dbp = dbp; c.wmax = wmax;
+    cudaError_t e = cudaMalloc(&c.d_tab, tab.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_base, base.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { free_tmem(c); return cuda_fail(e, "kernel 4 tables"); }
     c.ok = true;
     return DD_OK;
 }
@@ -250,7 +343,8 @@ static TuneKey tune_key(const dd_plan *p)
 static bool cfg_ok(const FastPlan *f, int k)
 {
     if (k < 0 || k >= kNumAllCfg) return false;
-    return k < kNumFastCfg ? f->cfg[k].ok : f->lane[k - kNumFastCfg].ok;
+    if (k < kNumFastCfg) return f->cfg[k].ok;
+    return k < kLaneEnd ? f->lane[k - kNumFastCfg].ok : f->tm[k - kLaneEnd].ok;
 }
 
 int fast_configure(dd_plan *p)
@@ -263,11 +357,15 @@ int fast_configure(dd_plan *p)
         rc = build_cfg(p, kFastCfg[k].tr, kFastCfg[k].nw, f->cfg[k]);
     for (int k = 0; k < kNumLaneCfg && rc == DD_OK; ++k)
         rc = build_lane(p, kLaneCfg[k].ti, kLaneCfg[k].dr, kLaneCfg[k].nw, kLaneCfg[k].minb, f->lane[k]);
+    for (int k = 0; k < kNumTmemCfg && rc == DD_OK; ++k)
+        rc = build_tmem(p, kTmemCfg[k].n, kTmemCfg[k].dbw, kTmemCfg[k].nw, f->tm[k]);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < kNumFastCfg && rc == DD_OK && e == cudaSuccess; ++k)
         if (f->cfg[k].ok) e = prepare_cfg(k, p->smem_optin);
     for (int k = 0; k < kNumLaneCfg && rc == DD_OK && e == cudaSuccess; ++k)
         if (f->lane[k].ok) e = prepare_lane(k, p->smem_optin);
+    for (int k = 0; k < kNumTmemCfg && rc == DD_OK && e == cudaSuccess; ++k)
+        if (f->tm[k].ok) e = prepare_tmem(k, p->smem_optin);
     if (rc == DD_OK && e == cudaSuccess) e = cudaMalloc(&f->d_err, sizeof(int));
     if (rc == DD_OK && e == cudaSuccess) e = cudaMemset(f->d_err, 0, sizeof(int));
     p->fast = f;
@@ -325,8 +423,34 @@ static int lane_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch
     return DD_OK;
 }
 
+static int tmem_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s)
+{
+    FastPlan *f = static_cast<FastPlan *>(p->fast);
+    TmemCfgData &c = f->tm[k];
+    const int tile = 32 * c.n;
+    const int64_t ntile = (p->nsamp_out + tile - 1) / tile;
+    if (ntile * c.nblk > INT32_MAX) return generic_execute(p, in, pitch, out, s);
+    const int64_t np = ntile * c.nblk;
+    int rc = ensure_partials_public(p, np);
+    if (rc) return rc;
+    TmemLaunch a;
+    a.in = in; a.pitch = pitch;
+    a.nsamp_in_al = (p->nsamp_in + f->al - 1) / f->al * f->al;
+    a.nchans = p->nchans; a.ndm = p->ndm; a.nout = p->nsamp_out;
+    a.tab = c.d_tab; a.base = c.d_base;
+    a.rs = c.rs; a.ch = c.ch; a.bar_off = c.bar_off; a.nblk = c.nblk; a.dbp = c.dbp; a.wmax = c.wmax;
+    a.ntile = ntile; a.dgroup = std::max(1, std::min(dgroup, c.nblk));
+    a.out = out; a.partials = p->d_partials; a.err = f->d_err; a.smem = c.smem;
+    cudaError_t e = launch_tmem(k, p->dtype, a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launch tmem_kernel");
+    p->n_partials = np;
+    p->stats_out = out;
+    return DD_OK;
+}
+
 static int fast_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s)
 {
+    if (k >= kLaneEnd) return tmem_run(p, k - kLaneEnd, dgroup, in, pitch, out, s);
     if (k >= kNumFastCfg) return lane_run(p, k - kNumFastCfg, dgroup, in, pitch, out, s);
     FastPlan *f = static_cast<FastPlan *>(p->fast);
     FastCfgData &c = f->cfg[k];
@@ -371,7 +495,8 @@ int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStre
     float best = 1e30f;
     int bk = f->active, bg = f->dgroup, rc = DD_OK;
     const int groups[] = {4, 8, 16};
-    for (int k = 0; k < kNumAllCfg && rc == DD_OK; ++k) {
+    // kernels 2 and 3; kernel 4 (slower on every plan measured) runs only on request
+    for (int k = 0; k < kLaneEnd && rc == DD_OK; ++k) {
         if (!cfg_ok(f, k)) continue;
         rc = fast_run(p, k, 8, in, pitch, out, s);             // warm-up (caches, clocks)
         for (int gi = 0; gi < 3 && rc == DD_OK; ++gi) {
@@ -419,9 +544,12 @@ int fast_get_tile(const dd_plan *p, int *cfg, int *dgroup, int *tr, int *nw)
     if (f->active < kNumFastCfg) {
         if (tr) *tr = f->cfg[f->active].tr;
         if (nw) *nw = f->cfg[f->active].nw;
-    } else {
+    } else if (f->active < kLaneEnd) {
         if (tr) *tr = f->lane[f->active - kNumFastCfg].ti;
         if (nw) *nw = f->lane[f->active - kNumFastCfg].nw;
+    } else {
+        if (tr) *tr = f->tm[f->active - kLaneEnd].n;
+        if (nw) *nw = f->tm[f->active - kLaneEnd].nw;
     }
     return DD_OK;
 }
@@ -429,7 +557,8 @@ int fast_get_tile(const dd_plan *p, int *cfg, int *dgroup, int *tr, int *nw)
 int fast_kernel_id(const dd_plan *p)
 {
     const FastPlan *f = static_cast<const FastPlan *>(p->fast);
-    return (f && f->active >= kNumFastCfg) ? 3 : 2;
+    if (!f || f->active < kNumFastCfg) return 2;
+    return f->active < kLaneEnd ? 3 : 4;
 }
 
 void fast_release(dd_plan *p)
@@ -438,6 +567,7 @@ void fast_release(dd_plan *p)
     if (!f) return;
     for (int k = 0; k < kNumFastCfg; ++k) free_cfg(f->cfg[k]);
     for (int k = 0; k < kNumLaneCfg; ++k) free_lane(f->lane[k]);
+    for (int k = 0; k < kNumTmemCfg; ++k) free_tmem(f->tm[k]);
     if (f->d_err) cudaFree(f->d_err);
     delete f;
     p->fast = nullptr;
