@@ -7,22 +7,26 @@
 // not; TMEM is: a tcgen05.ld reads any (warp-uniform) column offset of the
 // 32 TMEM lanes a warp owns.
 //
-// Block = 4*NQ warps.  Warp w uses TMEM lanes 32*(w%4).. (its lane quarter)
-// and DM trials (w/4)*DBW .. +DBW of the block's DB = NQ*DBW trials.  TMEM
-// lane L (0..127) owns the N consecutive output samples t0 + N*L .. +N-1 of
-// the block's 128*N-sample tile, for all DB trials.  Per channel c:
-//   fill:  the NQ warps of a quarter copy the window
-//          in[c][t0 + N*L + row0(c) + k], k < 8*kc8(c), shared -> TMEM
-//          (row0 = the smallest delay of the DM block, 16-byte aligned;
-//          N = 4 mod 8 makes the lanes' vector loads conflict-free);
-//   read:  for each own trial j, tcgen05.ld of N columns at the offset
-//          d(c,dm_j) - row0(c) gives in[c][t + d(c,dm_j)] for the lane's
+// Block = NW warps on one time tile of 32*N samples; lane l owns the N
+// consecutive outputs t0 + N*l .. +N-1, warp w the DM trials w*DBW .. +DBW
+// of the block's NW*DBW.  Per channel c each warp
+//   fill:  copies its window in[c][t0 + row0 + wbase + N*l + k], k < 8*kc8,
+//          shared -> registers -> TMEM (its lanes, its column range; row0 =
+//          the block's smallest delay, wbase = the warp's smallest delay above
+//          it; N = 4 mod 8 makes the lanes' vector loads conflict-free);
+//   read:  for each trial j, a tcgen05.ld of N columns at the offset
+//          d(c,dm_j) - row0 - wbase gives in[c][t + d(c,dm_j)] for the lane's
 //          N outputs, added into registers.
-// One staged word serves DB adds instead of one: the shared-memory traffic
-// per add drops to (span + N) / (N * DB), span = d(c,dm_last) - d(c,dm_first).
-// The window is double-buffered in TMEM (channel parity); a named barrier per
-// lane quarter separates a channel's fill from its reads, and the TMA stage
-// ring of input rows is the one of kernels 2 and 3.
+// One staged word serves DBW adds: shared-memory words per add drop to
+// (span + N) / (N * DBW), span = the warp's delay spread at channel c.  The
+// window is double-buffered in TMEM (channel parity) and the loads are
+// software-pipelined (the next batch of trials is in flight while the
+// previous one is added).  The TMA stage ring of input rows is the one of
+// kernels 2 and 3.
+//
+// Measured on GB300 this kernel is slower than kernel 3: the TMEM fill
+// (tcgen05.st) and the load round trip leave it latency-bound at the two
+// warps per scheduler that its accumulators allow.
 #pragma once
 
 #include "dd_fast_impl.cuh"
@@ -34,7 +38,7 @@ struct TmemLaunch {
     int64_t pitch, nsamp_in_al;
     int nchans, ndm;
     int64_t nout;
-    const int32_t *tab;    // [nblk][nchans][dbp]: DB column offsets, then kc8
+    const int32_t *tab;    // [nblk][nchans][dbp]: per warp {wbase, kc8, DBW column offsets}
     const int32_t *base;   // [nblk][nchans] row0 relative to the tile start (aligned)
     int rs, ch, bar_off, nblk, dbp, wmax;
     int64_t ntile;
@@ -47,13 +51,7 @@ struct TmemLaunch {
 // ------------------------------------------------------------- TMEM helpers
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void named_bar(int id, int nthreads)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
 
 // 8 columns of this thread's TMEM lane from 8 floats
 __device__ __forceinline__ void tc_st8(uint32_t taddr, const float (&w)[8])
