@@ -34,9 +34,15 @@ import synth  # noqa: E402
 
 METRIC = "DM-trial·samples/s"
 WORKLOAD = "lofar_f32"
-# ncu DRAM bytes (read + write) per de-dispersion launch, keyed by the kernel-2
+# ncu DRAM bytes (read + write) per de-dispersion launch, keyed by the
 # (tile configuration, raster group) the capture used
-PROFILED_TRAFFIC = {(1, 16): 21.01e9}
+PROFILED_TRAFFIC = {(5, 16): 25.63e9}
+
+# tile configurations of dd_plan_set_tile: (kernel, samples per thread or lane,
+# DM trials per thread or warp, warps per block)
+TILE_CONFIGS = {0: (2, 36, 4, 8), 1: (2, 20, 4, 12), 2: (2, 28, 4, 8), 3: (3, 16, 4, 8),
+                4: (3, 16, 8, 8), 5: (3, 16, 8, 4), 6: (3, 8, 16, 4), 7: (4, 20, 4, 8),
+                8: (4, 12, 8, 8)}
 
 
 def _pulses(wl, nout, seed):
@@ -217,7 +223,7 @@ def run_ours(args, rank, world, local_rank):
             ev[1].record(stream)
         return plan.search(out, capacity=1 << 16, stream=stream)
 
-    if plan.kernel == 2 and not args.no_autotune:
+    if not args.kernel and not args.no_autotune:
         plan.autotune(xin, wl.nsamp, out, stream)      # picks tile shape + raster (cached per shape)
     for _ in range(args.warmup):
         cands, total = step()
@@ -262,7 +268,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = units_per_rank * world / e2e_s
 
     kernel_id = plan.kernel
-    tile = plan.tile if kernel_id == 2 else None
+    tile = plan.tile if kernel_id in (2, 3, 4) else None
     plan.close()
     del out, xin
     if rank != 0:
@@ -273,17 +279,28 @@ def run_ours(args, rank, world, local_rank):
     adds = float(wl.ndm) * nout * wl.nchans
     achieved = adds / (ker_ms / 1e3) / 1e9             # G channel-adds / s
     peak = sm * 128 * sm_max * 1e6 / 1e9               # FP32 lanes x max clock
-    tile_s = (f", tile {tile[2]}x4 per thread, {tile[3]} warps, raster group {tile[1]}"
-              if tile else "")
+    tile_s = ""
+    if tile:
+        k, ns, nd, nw = TILE_CONFIGS[tile[0]]
+        per = "thread" if k == 2 else "lane"
+        tile_s = (f", tile config {tile[0]}: {ns} samples per {per} x {nd} DM trials per "
+                  f"{'thread' if k == 2 else 'warp'}, {nw} warps, raster group {tile[1]}")
     roof = {"bound": "alu", "kernel": f"dd kernel {kernel_id} (de-dispersion{tile_s})",
             "achieved": achieved, "peak": peak, "unit": "Gadd/s", "frac": achieved / peak,
             "peak_basis": f"{sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",
             # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
-            # capture summarised in profiles/dedisp_kernel2_lofar_f32.md; only for
+            # capture summarised in profiles/dedisp_kernel3_lofar_f32.md; only for
             # the tile it was taken with (null otherwise)
             "traffic": PROFILED_TRAFFIC.get(tuple(tile[:2])) if tile else None,
             "traffic_unit": "bytes per launch",
             "kernel_ms": ker_ms}
+    if kernel_id == 3:
+        # kernel 3 loads one shared-memory word per add: the shared-memory data
+        # path (32 words/clk/SM, 4 B x 32 banks) caps it at a quarter of the add peak
+        lds_peak = sm * 32 * sm_max * 1e6 / 1e9
+        roof["secondary"] = {"bound": "shared-memory words", "achieved": achieved, "peak": lds_peak,
+                             "unit": "Gword/s", "frac": achieved / lds_peak,
+                             "peak_basis": f"{sm} SMs x 32 banks x {sm_max:.0f} MHz"}
     if clk.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (sm * 128 * clk["sm_mhz"] * 1e6 / 1e9)
     line = {

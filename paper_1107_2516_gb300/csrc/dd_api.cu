@@ -272,17 +272,18 @@ int dd_plan_set_kernel(dd_plan *plan, int32_t kernel)
         }
         plan->kernel = 2; plan->kernel_req = 2; return DD_OK;
     }
-    if (kernel == 3) {
-        if (!plan->fast) return set_error(DD_ERR_ARG, "kernel 3 is not available for this plan");
-        int rc = fast_set_tile(plan, 3, 8);
+    if (kernel == 3 || kernel == 4) {
+        // the kernel's tile configurations, fastest measured first
+        static const int k3[] = {5, 3, 4, 6}, k4[] = {7, 8};
+        const int *cfg = kernel == 3 ? k3 : k4;
+        const int n = kernel == 3 ? 4 : 2;
+        int rc = set_error(DD_ERR_ARG, "kernel %d is not available for this plan", kernel);
+        for (int i = 0; plan->fast && i < n && rc != DD_OK; ++i) {
+            rc = fast_set_tile(plan, cfg[i], 8);
+            if (rc != DD_OK) set_error(DD_ERR_ARG, "kernel %d is not available for this plan", kernel);
+        }
         if (rc) return rc;
-        plan->kernel = 2; plan->kernel_req = 3; return DD_OK;
-    }
-    if (kernel == 4) {
-        if (!plan->fast) return set_error(DD_ERR_ARG, "kernel 4 is not available for this plan");
-        int rc = fast_set_tile(plan, 7, 8);
-        if (rc) return rc;
-        plan->kernel = 2; plan->kernel_req = 4; return DD_OK;
+        plan->kernel = 2; plan->kernel_req = kernel; return DD_OK;
     }
     return set_error(DD_ERR_ARG, "unknown kernel %d", kernel);
 }

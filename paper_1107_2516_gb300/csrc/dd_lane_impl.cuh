@@ -113,9 +113,15 @@ __global__ void __launch_bounds__(NW * 32, MINB) lane_kernel(LaneLaunch a)
         const int32_t *so = soffs + (size_t)buf * ch * kDmBlk + warp * DR;
         for (int cc = 0; cc < cn; ++cc) {
             const Tin *r = srow + (size_t)cc * rs;
+            // the warp's DR offsets: uniform 16-byte loads, one shared-memory
+            // wavefront per 4 offsets (the data path is the kernel's bound)
             int o[DR];
+            static_assert(DR % 4 == 0, "offsets are loaded 4 at a time");
 #pragma unroll
-            for (int j = 0; j < DR; ++j) o[j] = so[cc * kDmBlk + j];
+            for (int j = 0; j < DR; j += 4) {
+                const int4 v = *reinterpret_cast<const int4 *>(so + cc * kDmBlk + j);
+                o[j] = v.x; o[j + 1] = v.y; o[j + 2] = v.z; o[j + 3] = v.w;
+            }
 #pragma unroll
             for (int j = 0; j < DR; ++j) {
                 const Tin *p = r + o[j];

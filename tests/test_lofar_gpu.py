@@ -54,20 +54,51 @@ def lofar():
 def test_delay_table_and_kernel(lofar):
     assert lofar["plan"].maxshift == lofar["m"] == 20397
     assert np.array_equal(lofar["plan"].delays().astype(np.int64), lofar["d"])
-    assert lofar["plan"].kernel == 2
+    assert lofar["plan"].kernel in (2, 3)       # autotuned: register-blocked or lane-interleaved
 
 
-def test_sampled_points(lofar):
-    x, d, nout, out = lofar["x"], lofar["d"], lofar["nout"], lofar["out"]
-    rng = np.random.default_rng(123)
-    dms = list(rng.integers(0, WL.ndm, 3000)) + [0, 31, 32, 1999, 1999, 1998, 0]
-    ts = list(rng.integers(0, nout, 3000)) + [0, 1151, 1152, nout - 1, 0, nout - 1152, nout - 1]
+def _check_sampled(x, d, nout, out, tile_samples, seed):
+    # random points plus the tile and DM-block edges of the launch configuration
+    rng = np.random.default_rng(seed)
+    tt = tile_samples
+    dms = list(rng.integers(0, WL.ndm, 3000)) + [0, 31, 32, 47, 48, 63, 64, 1999, 1999, 1998, 0]
+    ts = list(rng.integers(0, nout, 3000)) + [0, tt - 1, tt, 2 * tt - 1, 2 * tt, 3 * tt,
+                                              nout - 1, 0, nout - tt, nout - 1, nout - 2]
     idx_dm = torch.tensor(dms, device="cuda")
     idx_t = torch.tensor(ts, device="cuda")
     got = out[idx_dm, idx_t].cpu().numpy().astype(np.float64)
     for k, (i, t) in enumerate(zip(dms, ts)):
         ref = oracle.point_f32(x, d[i], int(t))
         assert abs(got[k] - ref) <= fp_tol(WL.nchans), (i, t, got[k], ref)
+
+
+def test_sampled_points(lofar):
+    x, d, nout, out = lofar["x"], lofar["d"], lofar["nout"], lofar["out"]
+    _check_sampled(x, d, nout, out, 32 * lofar["plan"].tile[2], 123)
+
+
+@pytest.mark.parametrize("cfg", [7, 8])
+def test_kernel4_full_size(lofar, cfg):
+    # the tensor-memory kernel on the full plan: sampled points and one whole row
+    x, d, nout = lofar["x"], lofar["d"], lofar["nout"]
+    wl = WL
+    plan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, wl.sigma,
+                   dd.DD_F32, wl.nsamp)
+    plan.set_kernel(4)
+    plan.set_tile(cfg, 16)
+    assert plan.kernel == 4
+    xin = torch.from_numpy(x).cuda()
+    out = torch.empty(wl.ndm * nout, dtype=torch.float32, device="cuda")
+    plan.execute(xin, wl.nsamp, out)
+    plan.search(out, capacity=1 << 20)
+    torch.cuda.synchronize()
+    out = out.view(wl.ndm, nout)
+    _check_sampled(x, d, nout, out, 32 * plan.tile[2], 321 + cfg)
+    ref = oracle.row_f32(x, d[1999], nout)
+    assert np.max(np.abs(out[1999].cpu().numpy().astype(np.float64) - ref)) <= fp_tol(wl.nchans)
+    mu, _ = plan.stats()
+    assert abs(mu - lofar["mu"]) <= 1e-6 * math.sqrt(wl.nchans)
+    plan.close()
 
 
 @pytest.mark.parametrize("row", [0, 777, 1999])
