@@ -12,6 +12,7 @@ Paper passages followed (Magro et al. 2011):
   Section 3, Eq. 2         maximum shift             -> delays(), maxshift_eq2()
   Section 3.1              brute-force sum           -> dedisperse()
   Section 3 (output thread) mean, sigma, n-sigma test -> stats(), search()
+  Section 3.2              subband de-dispersion     -> subband_tables(), subband_dedisperse()
 """
 from __future__ import annotations
 
@@ -76,6 +77,14 @@ def _load():
         for name in ("oracle_search_f64", "oracle_search_i64"):
             getattr(lib, name).restype = i64
             getattr(lib, name).argtypes = [vp, i64, i64, vp, i64, f64, f64, f64, vp, i64]
+        lib.oracle_subband_tables.restype = C.c_int
+        lib.oracle_subband_tables.argtypes = [i64, f64, f64, f64, vp, i64, i64, i64, vp, vp, vp,
+                                              C.POINTER(i64)]
+        for name in ("oracle_subband_f32", "oracle_subband_f16", "oracle_subband_u8"):
+            getattr(lib, name).restype = None
+            getattr(lib, name).argtypes = [vp, i64, i64, i64, vp, vp, i64, i64, i64, vp]
+        lib.oracle_subband_point_f32.restype = f64
+        lib.oracle_subband_point_f32.argtypes = [vp, i64, i64, i64, vp, vp, i64, i64, i64]
         _lib = lib
         return lib
 
@@ -192,3 +201,65 @@ def search(out: np.ndarray, widths, mu: float, sigma: float, k: float,
     if n > cap:
         raise OverflowError(f"oracle search found {n} candidates > cap {cap}")
     return cands[:n].copy()
+
+
+def subband_tables(nchans: int, fch1: float, foff: float, tsamp: float, dm_list, G: int,
+                   nsub: int) -> tuple:
+    """Section 3.2 subband plan: (nominal DMs [K], d1 [K][nchans], d2 [ndm][nsub], maxshift).
+
+    Fine DMs in consecutive groups of G around nominal DM k (the midpoint of
+    the group's first and last DM); nsub equal subbands of consecutive
+    channels; d1 = stage-1 delay of each channel at the nominal DM relative to
+    its subband's highest-frequency channel; d2 = stage-2 delay of each
+    subband (its highest-frequency channel) at each fine DM."""
+    dm = np.ascontiguousarray(np.asarray(dm_list, dtype=np.float64))
+    K = (dm.size + G - 1) // G
+    nominal = np.empty(K, np.float64)
+    d1 = np.empty((K, nchans), np.int64)
+    d2 = np.empty((dm.size, nsub), np.int64)
+    m = C.c_int64(0)
+    rc = _load().oracle_subband_tables(nchans, fch1, foff, tsamp, _p(dm), dm.size, G, nsub,
+                                       _p(nominal), _p(d1), _p(d2), C.byref(m))
+    if rc != 0:
+        raise ValueError("oracle_subband_tables: invalid arguments")
+    return nominal, d1, d2, int(m.value)
+
+
+def subband_dedisperse(data: np.ndarray, d1: np.ndarray, d2: np.ndarray, G: int,
+                       nout: int) -> np.ndarray:
+    """Two-stage subband sum (Section 3.2); [ndm][nout] float64 (int64 for uint8)."""
+    lib = _load()
+    data = np.ascontiguousarray(data)
+    d1 = np.ascontiguousarray(d1, dtype=np.int64)
+    d2 = np.ascontiguousarray(d2, dtype=np.int64)
+    nchans, pitch = data.shape
+    ndm, nsub = d2.shape
+    assert d1.shape[1] == nchans and nchans % nsub == 0
+    cs = nchans // nsub
+    need = 0
+    for j in range(ndm):
+        e = d2[j][np.arange(nchans) // cs] + d1[j // G]
+        need = max(need, int(e.max()))
+    if nout < 0 or (nout > 0 and need + nout > pitch):
+        raise ValueError("input too short for nout + maxshift")
+    if data.dtype == np.float32:
+        out = np.empty((ndm, nout), np.float64)
+        lib.oracle_subband_f32(_p(data), pitch, nchans, nsub, _p(d1), _p(d2), G, ndm, nout, _p(out))
+    elif data.dtype == np.uint16:
+        out = np.empty((ndm, nout), np.float64)
+        lib.oracle_subband_f16(_p(data), pitch, nchans, nsub, _p(d1), _p(d2), G, ndm, nout, _p(out))
+    elif data.dtype == np.uint8:
+        out = np.empty((ndm, nout), np.int64)
+        lib.oracle_subband_u8(_p(data), pitch, nchans, nsub, _p(d1), _p(d2), G, ndm, nout, _p(out))
+    else:
+        raise TypeError(f"unsupported input dtype {data.dtype}")
+    return out
+
+
+def subband_point_f32(data: np.ndarray, d1: np.ndarray, d2: np.ndarray, G: int, j: int,
+                      t: int) -> float:
+    data = np.ascontiguousarray(data, dtype=np.float32)
+    d1 = np.ascontiguousarray(d1, dtype=np.int64)
+    d2 = np.ascontiguousarray(d2, dtype=np.int64)
+    return float(_load().oracle_subband_point_f32(_p(data), data.shape[1], data.shape[0],
+                                                  d2.shape[1], _p(d1), _p(d2), G, int(j), int(t)))

@@ -20,6 +20,8 @@
  *     input samples.
  *   - Section 3.1: brute force, each output sample is the sum over all
  *     channels of the input shifted by that channel's delay.
+ *   - Section 3.2: subband de-dispersion, the two-stage approximation (at the
+ *     end of this file).
  *   - Section 3 (output thread): mean and standard deviation over the whole
  *     processed buffer, an n-sigma threshold, every value above it emitted as
  *     (time, DM, intensity).  The search generalises the single sample to
@@ -346,4 +348,149 @@ ORACLE_API int64_t oracle_search_i64(const int64_t *out, int64_t ndm, int64_t no
         }
     }
     return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Section 3.2: subband de-dispersion.                                       */
+/*                                                                          */
+/* The fine DM list is split into consecutive groups of G trials, each      */
+/* centred on a nominal DM; the channels are split into nsub subbands of    */
+/* nchans/nsub consecutive channels.                                        */
+/*   stage 1: for every nominal DM k and subband s, the subband's channels  */
+/*            are shifted by their delay at the nominal DM minus the delay  */
+/*            of the subband's highest-frequency channel, and summed:       */
+/*              I[k][s][t] = sum_{c in s} in[c][t + d1(k,c)],               */
+/*              d1(k,c) = d(c, D_k) - d(ref(s), D_k);                       */
+/*   stage 2: every fine DM j of group k is de-dispersed by brute force     */
+/*            over the subband series, each subband shifted by the delay    */
+/*            of its highest-frequency channel at the fine DM:              */
+/*              out[j][t] = sum_s I[k][s][t + d2(j,s)],  d2(j,s) = d(ref(s), dm_j). */
+/* Readings: the nominal DM of a group is the midpoint of its first and     */
+/* last fine DM; subbands are equal groups of consecutive channels; d() is  */
+/* the rounded Eq. 1 delay of the brute-force path, so at a fine DM whose   */
+/* delays equal the nominal DM's the result is the brute-force sum.         */
+/* ------------------------------------------------------------------------ */
+
+/* Highest-frequency channel of subband s (cs channels per subband). */
+static int64_t subband_ref(double foff, int64_t s, int64_t cs)
+{
+    return foff < 0.0 ? s * cs : s * cs + cs - 1;
+}
+
+/* Tables of the two stages.  nominal[K]; d1[K][nchans]; d2[ndm][nsub];
+ * *maxshift = max over (j, c) of d2(j, sub(c)) + d1(k(j), c).
+ * Returns 0, or -1 for invalid arguments. */
+ORACLE_API int oracle_subband_tables(int64_t nchans, double fch1, double foff, double tsamp_s,
+                                     const double *dm_list, int64_t ndm, int64_t G, int64_t nsub,
+                                     double *nominal, int64_t *d1, int64_t *d2, int64_t *maxshift)
+{
+    if (G < 1 || nsub < 1 || nchans % nsub != 0)
+        return -1;
+    const int64_t cs = nchans / nsub;
+    const int64_t K = (ndm + G - 1) / G;
+    int64_t m_fine = 0, m_nom = 0;
+    int64_t *fine = (int64_t *)malloc(sizeof(int64_t) * ndm * nchans);
+    int64_t *nom = (int64_t *)malloc(sizeof(int64_t) * K * nchans);
+    if (!fine || !nom) { free(fine); free(nom); return -1; }
+    int rc = oracle_delays(nchans, fch1, foff, tsamp_s, dm_list, ndm, fine, &m_fine);
+    if (rc == 0) {
+        for (int64_t k = 0; k < K; ++k) {
+            const int64_t j0 = k * G;
+            const int64_t j1 = (j0 + G < ndm ? j0 + G : ndm) - 1;
+            nominal[k] = 0.5 * (dm_list[j0] + dm_list[j1]);
+        }
+        rc = oracle_delays(nchans, fch1, foff, tsamp_s, nominal, K, nom, &m_nom);
+    }
+    if (rc == 0) {
+        for (int64_t k = 0; k < K; ++k)
+            for (int64_t c = 0; c < nchans; ++c) {
+                const int64_t r = subband_ref(foff, c / cs, cs);
+                d1[k * nchans + c] = nom[k * nchans + c] - nom[k * nchans + r];
+            }
+        for (int64_t j = 0; j < ndm; ++j)
+            for (int64_t s = 0; s < nsub; ++s)
+                d2[j * nsub + s] = fine[j * nchans + subband_ref(foff, s, cs)];
+        int64_t m = 0;
+        for (int64_t j = 0; j < ndm; ++j)
+            for (int64_t c = 0; c < nchans; ++c) {
+                const int64_t e = d2[j * nsub + c / cs] + d1[(j / G) * nchans + c];
+                if (e > m)
+                    m = e;
+            }
+        *maxshift = m;
+    }
+    free(fine);
+    free(nom);
+    return rc;
+}
+
+/* Stage 1 then stage 2 for one output sample of fine DM j: the subband sums
+ * (ascending channel) and then their sum (ascending subband), in double. */
+static double subband_point(const float *in_f32, const uint16_t *in_f16, int64_t pitch,
+                            int64_t nchans, int64_t nsub, const int64_t *d1, const int64_t *d2,
+                            int64_t G, int64_t j, int64_t t)
+{
+    const int64_t cs = nchans / nsub;
+    const int64_t *r1 = d1 + (j / G) * nchans;
+    double out = 0.0;
+    for (int64_t s = 0; s < nsub; ++s) {
+        const int64_t tt = t + d2[j * nsub + s];
+        double sub = 0.0;
+        for (int64_t c = s * cs; c < (s + 1) * cs; ++c) {
+            const int64_t i = c * pitch + tt + r1[c];
+            sub += in_f32 ? (double)in_f32[i] : oracle_half_to_double(in_f16[i]);
+        }
+        out += sub;
+    }
+    return out;
+}
+
+ORACLE_API void oracle_subband_f32(const float *in, int64_t pitch, int64_t nchans, int64_t nsub,
+                                   const int64_t *d1, const int64_t *d2, int64_t G, int64_t ndm,
+                                   int64_t nout, double *out)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < ndm; ++j)
+        for (int64_t t = 0; t < nout; ++t)
+            out[j * nout + t] = subband_point(in, NULL, pitch, nchans, nsub, d1, d2, G, j, t);
+}
+
+ORACLE_API void oracle_subband_f16(const uint16_t *in, int64_t pitch, int64_t nchans, int64_t nsub,
+                                   const int64_t *d1, const int64_t *d2, int64_t G, int64_t ndm,
+                                   int64_t nout, double *out)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < ndm; ++j)
+        for (int64_t t = 0; t < nout; ++t)
+            out[j * nout + t] = subband_point(NULL, in, pitch, nchans, nsub, d1, d2, G, j, t);
+}
+
+ORACLE_API void oracle_subband_u8(const uint8_t *in, int64_t pitch, int64_t nchans, int64_t nsub,
+                                  const int64_t *d1, const int64_t *d2, int64_t G, int64_t ndm,
+                                  int64_t nout, int64_t *out)
+{
+    const int64_t cs = nchans / nsub;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < ndm; ++j) {
+        const int64_t *r1 = d1 + (j / G) * nchans;
+        for (int64_t t = 0; t < nout; ++t) {
+            int64_t acc = 0;
+            for (int64_t s = 0; s < nsub; ++s) {
+                const int64_t tt = t + d2[j * nsub + s];
+                int64_t sub = 0;
+                for (int64_t c = s * cs; c < (s + 1) * cs; ++c)
+                    sub += (int64_t)in[c * pitch + tt + r1[c]];
+                acc += sub;
+            }
+            out[j * nout + t] = acc;
+        }
+    }
+}
+
+/* One output sample (float32 input), for sampled checks at full size. */
+ORACLE_API double oracle_subband_point_f32(const float *in, int64_t pitch, int64_t nchans,
+                                           int64_t nsub, const int64_t *d1, const int64_t *d2,
+                                           int64_t G, int64_t j, int64_t t)
+{
+    return subband_point(in, NULL, pitch, nchans, nsub, d1, d2, G, j, t);
 }
