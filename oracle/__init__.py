@@ -213,6 +213,8 @@ def subband_tables(nchans: int, fch1: float, foff: float, tsamp: float, dm_list,
     its subband's highest-frequency channel; d2 = stage-2 delay of each
     subband (its highest-frequency channel) at each fine DM."""
     dm = np.ascontiguousarray(np.asarray(dm_list, dtype=np.float64))
+    if G < 1 or nsub < 1:
+        raise ValueError("oracle_subband_tables: invalid arguments")
     K = (dm.size + G - 1) // G
     nominal = np.empty(K, np.float64)
     d1 = np.empty((K, nchans), np.int64)
