@@ -321,6 +321,69 @@ DD_API int dd_server_memory(dd_server *server, int64_t *used, int64_t *budget);
  * wrong values; calls ordered on one stream are safe. */
 DD_API int dd_stats_f32_noalloc(const float *x_dev, int64_t n, double *mu_sigma_dev, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Subband de-dispersion (Section 3.2): the paper's two-stage approximation
+ * of the Section 3.1 sum, for fewer adds per output.
+ *
+ * The fine DM list (dm_list, ndm trials) is split into consecutive groups of
+ * dms_per_nominal trials (the last group may be shorter); each group's
+ * nominal DM is the midpoint of its first and last trial.  The nchans
+ * channels are split into nsub subbands of nchans/nsub consecutive channels
+ * (nsub must divide nchans); ref(s) is subband s's highest-frequency channel.
+ * With d(c, DM) the Eq. 1 delay of dd_plan_create:
+ *   stage 1  I[s][k][t] = sum_{c in s} in[c][t + d(c, D_k) - d(ref(s), D_k)]
+ *            (each subband partially de-dispersed at nominal DM D_k),
+ *   stage 2  out[j][t]  = sum_s I[s][k(j)][t + d(ref(s), dm_j)]
+ *            (brute force over the subbands at each fine DM of group k(j)).
+ * A fine DM whose delays equal its nominal DM's gets exactly the brute-force
+ * sum; elsewhere each channel's effective delay differs from d(c, dm_j) by at
+ * most |dm_j - D_k| x (its delay per unit DM minus ref(s)'s) + 2 samples,
+ * the smearing the paper trades for speed.  Work per output sample:
+ * nchans/dms_per_nominal + nsub adds instead of nchans.
+ *
+ * maxshift = max over (j, c) of the effective delay; nsamp_out = nsamp_in -
+ * maxshift.  Output layout and dtype are those of dd_execute.  The plan owns
+ * the intermediate series (nsub x n_nominal x L float32, L = nsamp_out + the
+ * largest stage-2 delay rounded up to 4; allocated on the first execute,
+ * size from dd_subband_plan_info) and the search scratch.  Input rows must be
+ * 16-byte aligned (pointer and pitch); other arguments are checked as in
+ * dd_plan_create.  Errors: DD_ERR_ARG (arguments, rows too long for shared
+ * memory), DD_ERR_NOMEM, DD_ERR_CUDA. */
+typedef struct dd_subband_plan dd_subband_plan;
+
+DD_API int dd_subband_plan_create(int32_t nchans, double fch1_mhz, double foff_mhz, double tsamp_s,
+                                  const double *dm_list, int32_t ndm, int32_t dms_per_nominal,
+                                  int32_t nsub, const int32_t *boxcar_widths, int32_t nwidths,
+                                  double sigma, int32_t in_dtype, int64_t nsamp_in,
+                                  dd_subband_plan **plan_out);
+
+/* Synchronises the device, then frees everything the plan owns. */
+DD_API int dd_subband_plan_destroy(dd_subband_plan *plan);
+
+/* Plan geometry; every pointer may be NULL.  nominal_dms: [n_nominal];
+ * stage1_delays: [n_nominal][nchans] (d(c,D_k) - d(ref(s),D_k));
+ * stage2_delays: [ndm][nsub] (d(ref(s), dm_j)); work_bytes: the intermediate
+ * series' device bytes.  Host buffers, caller-owned. */
+DD_API int dd_subband_plan_info(const dd_subband_plan *plan, int32_t *n_nominal, int64_t *maxshift,
+                                int64_t *nsamp_out, double *nominal_dms, int32_t *stage1_delays,
+                                int32_t *stage2_delays, int64_t *work_bytes);
+
+/* Both stages, asynchronously on `stream` (in: [nchans][in_pitch] device,
+ * out: [ndm][nsamp_out] device, as dd_execute), plus the per-block
+ * statistics partials of out that dd_subband_search uses. */
+DD_API int dd_subband_execute(dd_subband_plan *plan, const void *in_dev, int64_t in_pitch,
+                              void *out_dev, void *stream);
+
+/* dd_search on the subband output (Section 3 output stage: global mu/sigma,
+ * boxcar n-sigma test, candidates sorted by (dm, t, width)); synchronises
+ * `stream`.  DD_ERR_OVERFLOW as dd_search; DD_ERR_TIMEOUT if a kernel of the
+ * last execute gave up waiting for its input copies. */
+DD_API int dd_subband_search(dd_subband_plan *plan, const void *out_dev, dd_candidate *cand_host,
+                             int64_t capacity, int64_t *n_found, void *stream);
+
+/* mu and sigma used by the last dd_subband_search. */
+DD_API int dd_subband_last_stats(const dd_subband_plan *plan, double *mu, double *sigma);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 DD_API const char *dd_last_error(void);
 

@@ -37,8 +37,8 @@ size_t in_elem_bytes(dd_dtype t)
 // Evaluated as ((4.15e6*DM) * (1/f^2 - 1/f_top^2)) / (tsamp*1e3) in double,
 // left to right; this file is compiled with FMA contraction off so the
 // rounding of every step is fixed.  Rounded half away from zero.
-static long long delay_samples(double fch1, double foff, int nchans, double tsamp_s,
-                               double dm, int c)
+long long delay_samples(double fch1, double foff, int nchans, double tsamp_s,
+                        double dm, int c)
 {
     const double f_top = (foff < 0.0) ? fch1 + 0.0 * foff : fch1 + (double)(nchans - 1) * foff;
     const double f = fch1 + (double)c * foff;
@@ -142,6 +142,18 @@ int dd_plan_create(int32_t nchans, double fch1_mhz, double foff_mhz, double tsam
                    const int32_t *boxcar_widths, int32_t nwidths, double sigma_k,
                    int32_t in_dtype, int64_t nsamp_in, dd_plan **plan_out)
 {
+    return dd::plan_create(nchans, fch1_mhz, foff_mhz, tsamp_s, dm_list, ndm, boxcar_widths, nwidths,
+                           sigma_k, in_dtype, nsamp_in, true, plan_out);
+}
+
+}  // extern "C"
+
+namespace dd {
+
+int plan_create(int32_t nchans, double fch1_mhz, double foff_mhz, double tsamp_s,
+                const double *dm_list, int32_t ndm, const int32_t *boxcar_widths, int32_t nwidths,
+                double sigma_k, int32_t in_dtype, int64_t nsamp_in, bool kernels, dd_plan **plan_out)
+{
     g_err[0] = 0;
     if (!plan_out) return set_error(DD_ERR_ARG, "plan_out is NULL");
     *plan_out = nullptr;
@@ -230,13 +242,19 @@ int dd_plan_create(int32_t nchans, double fch1_mhz, double foff_mhz, double tsam
         if (e != cudaSuccess) { int rc = cuda_fail(e, "plan scratch"); free_plan(p); return rc; }
     }
     int rc = ensure_cands(p, 1 << 16);
-    if (rc == DD_OK) rc = generic_configure(p);
-    if (rc == DD_OK) rc = fast_configure(p);   // may leave kernel 2 unavailable
+    if (kernels) {
+        if (rc == DD_OK) rc = generic_configure(p);
+        if (rc == DD_OK) rc = fast_configure(p);   // may leave the tiled kernels unavailable
+    }
     if (rc != DD_OK) { free_plan(p); return rc; }
     p->kernel = p->fast ? 2 : 1;
     *plan_out = p;
     return DD_OK;
 }
+
+}  // namespace dd
+
+extern "C" {
 
 int dd_plan_destroy(dd_plan *plan)
 {

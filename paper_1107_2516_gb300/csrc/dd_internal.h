@@ -91,6 +91,15 @@ namespace dd {
 int set_error(int code, const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
 
+// dd_api.cu: Eq. 1 delay in samples (rounded), and plan creation; with
+// kernels == false the plan gets its delay table and search scratch only
+// (no de-dispersion kernel tables), for composite plans that run their own
+// kernels and reuse the search.
+long long delay_samples(double fch1, double foff, int nchans, double tsamp_s, double dm, int c);
+int plan_create(int32_t nchans, double fch1_mhz, double foff_mhz, double tsamp_s,
+                const double *dm_list, int32_t ndm, const int32_t *boxcar_widths, int32_t nwidths,
+                double sigma_k, int32_t in_dtype, int64_t nsamp_in, bool kernels, dd_plan **plan_out);
+
 size_t in_elem_bytes(dd_dtype t);
 
 // dd_kernels.cu

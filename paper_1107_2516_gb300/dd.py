@@ -33,7 +33,8 @@ EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "d
            "dd_batch_launch", "dd_batch_results", "dd_batch_autotune", "dd_batch_info",
            "dd_server_create", "dd_server_destroy", "dd_server_add_beam", "dd_server_remove_beam",
            "dd_server_submit", "dd_server_poll", "dd_server_candidates", "dd_server_beam_info",
-           "dd_server_memory")
+           "dd_server_memory", "dd_subband_plan_create", "dd_subband_plan_destroy",
+           "dd_subband_plan_info", "dd_subband_execute", "dd_subband_search", "dd_subband_last_stats")
 
 DD_PRIMING = 7
 
@@ -101,6 +102,13 @@ def load(path: Optional[str] = None):
             "dd_server_memory": (C.c_int, [vp, P64, P64]),
             "dd_plan_get_tile": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                            C.POINTER(i32)]),
+            "dd_subband_plan_create": (C.c_int, [i32, f64, f64, f64, vp, i32, i32, i32, vp, i32, f64,
+                                                 i32, i64, C.POINTER(vp)]),
+            "dd_subband_plan_destroy": (C.c_int, [vp]),
+            "dd_subband_plan_info": (C.c_int, [vp, C.POINTER(i32), P64, P64, vp, vp, vp, P64]),
+            "dd_subband_execute": (C.c_int, [vp, vp, i64, vp, vp]),
+            "dd_subband_search": (C.c_int, [vp, vp, vp, i64, P64, vp]),
+            "dd_subband_last_stats": (C.c_int, [vp, C.POINTER(f64), C.POINTER(f64)]),
             "dd_last_error": (C.c_char_p, []),
             "dd_version": (C.c_char_p, []),
         }
@@ -458,6 +466,95 @@ class Plan:
     def close(self):
         if self.handle:
             dd_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ subband (Section 3.2)
+
+def dd_subband_plan_create(nchans, fch1, foff, tsamp, dm_list, dms_per_nominal, nsub, boxcar_widths,
+                           sigma, in_dtype, nsamp_in) -> int:
+    dm = np.ascontiguousarray(np.asarray(dm_list, dtype=np.float64))
+    w = np.ascontiguousarray(np.asarray(boxcar_widths, dtype=np.int32))
+    out = C.c_void_p()
+    _check(load().dd_subband_plan_create(int(nchans), float(fch1), float(foff), float(tsamp),
+                                         dm.ctypes.data, int(dm.size), int(dms_per_nominal), int(nsub),
+                                         w.ctypes.data, int(w.size), float(sigma), int(in_dtype),
+                                         int(nsamp_in), C.byref(out)))
+    return int(out.value)
+
+
+def dd_subband_plan_destroy(plan: int) -> None:
+    _check(load().dd_subband_plan_destroy(plan))
+
+
+def dd_subband_plan_info(plan: int, ndm: int = 0, nchans: int = 0, nsub: int = 0, tables=False):
+    """(n_nominal, maxshift, nsamp_out, work_bytes[, nominal, stage1 [K][nchans], stage2 [ndm][nsub]])."""
+    k, m, n, wb = C.c_int32(), C.c_int64(), C.c_int64(), C.c_int64()
+    lib = load()
+    _check(lib.dd_subband_plan_info(plan, C.byref(k), C.byref(m), C.byref(n), None, None, None,
+                                    C.byref(wb)))
+    base = (int(k.value), int(m.value), int(n.value), int(wb.value))
+    if not tables:
+        return base
+    nom = np.empty(base[0], np.float64)
+    d1 = np.empty((base[0], nchans), np.int32)
+    d2 = np.empty((ndm, nsub), np.int32)
+    _check(lib.dd_subband_plan_info(plan, None, None, None, _ptr(nom), _ptr(d1), _ptr(d2), None))
+    return base + (nom, d1, d2)
+
+
+def dd_subband_execute(plan: int, in_dev, in_pitch: int, out_dev, stream=None) -> None:
+    _check(load().dd_subband_execute(plan, _ptr(in_dev), int(in_pitch), _ptr(out_dev), _stream(stream)))
+
+
+def dd_subband_search(plan: int, out_dev, capacity: int = 1 << 16, stream=None, allow_overflow=False):
+    cands = np.zeros(max(capacity, 1), dtype=CANDIDATE_DTYPE)
+    n = C.c_int64()
+    _check(load().dd_subband_search(plan, _ptr(out_dev), cands.ctypes.data, int(capacity), C.byref(n),
+                                    _stream(stream)), allow=(DD_ERR_OVERFLOW,) if allow_overflow else ())
+    total = int(n.value)
+    return cands[:min(total, capacity)].copy(), total
+
+
+def dd_subband_last_stats(plan: int):
+    mu, sg = C.c_double(), C.c_double()
+    _check(load().dd_subband_last_stats(plan, C.byref(mu), C.byref(sg)))
+    return float(mu.value), float(sg.value)
+
+
+class SubbandPlan:
+    """Owning wrapper around a dd_subband_plan handle (marshalling only)."""
+
+    def __init__(self, nchans, fch1, foff, tsamp, dm_list, dms_per_nominal, nsub, boxcar_widths, sigma,
+                 in_dtype, nsamp_in):
+        self.nchans, self.ndm, self.nsub = int(nchans), len(dm_list), int(nsub)
+        self.in_dtype = int(in_dtype)
+        self.handle = dd_subband_plan_create(nchans, fch1, foff, tsamp, dm_list, dms_per_nominal, nsub,
+                                             boxcar_widths, sigma, in_dtype, nsamp_in)
+        self.n_nominal, self.maxshift, self.nsamp_out, self.work_bytes = dd_subband_plan_info(self.handle)
+
+    def tables(self):
+        """(nominal DMs, stage-1 delays [K][nchans], stage-2 delays [ndm][nsub])."""
+        return dd_subband_plan_info(self.handle, self.ndm, self.nchans, self.nsub, tables=True)[4:]
+
+    def execute(self, in_dev, in_pitch, out_dev, stream=None):
+        dd_subband_execute(self.handle, in_dev, in_pitch, out_dev, stream)
+
+    def search(self, out_dev, capacity=1 << 16, stream=None, allow_overflow=False):
+        return dd_subband_search(self.handle, out_dev, capacity, stream, allow_overflow)
+
+    def stats(self):
+        return dd_subband_last_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            dd_subband_plan_destroy(self.handle)
             self.handle = 0
 
     def __del__(self):
