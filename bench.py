@@ -534,15 +534,102 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_subband(args):
+    """Section 3.2 subband de-dispersion of the LOFAR-like beam (1024 channels
+    in 32 subbands, 2000 fine DMs in groups of 24 = 1.2 pc/cm3 per nominal DM)
+    against the brute-force path on the same input: throughput, adds, and the
+    S/N of the 16 injected pulses found by each.  Prints one JSON line (mode
+    "subband")."""
+    import torch
+    import paper_1107_2516_gb300 as dd
+    from paper_1107_2516_gb300 import build as ddbuild
+
+    ddbuild.build()
+    dd.load()
+    wl = synth.workload(WORKLOAD)
+    G, nsub = args.dms_per_nominal, args.nsub
+    sp = dd.SubbandPlan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, G, nsub, wl.widths, wl.sigma,
+                        dd.DD_F32, wl.nsamp)
+    bf = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, wl.sigma, dd.DD_F32,
+                 wl.nsamp)
+    x = synth.noise_f32(wl.nchans, wl.nsamp, seed=wl.seed + 7)
+    pulses = _pulses(wl, min(sp.nsamp_out, bf.nsamp_out), seed=wl.seed + 7)
+    ptab = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, [p.dm for p in pulses], [1], 6.0, dd.DD_F32,
+                   wl.nsamp)
+    lookup = {p.dm: ptab.delays().astype(np.int64)[i] for i, p in enumerate(pulses)}
+    ptab.close()
+    synth.inject_pulses(x, pulses, lambda dm: lookup[dm], wl.nsamp)
+    xin = torch.from_numpy(x).cuda()
+    stream = torch.cuda.current_stream()
+    out_s = torch.empty(wl.ndm * sp.nsamp_out, device="cuda")
+    out_b = torch.empty(wl.ndm * bf.nsamp_out, device="cuda")
+    bf.autotune(xin, wl.nsamp, out_b, stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def step(plan, out):
+        ev[0].record(stream)
+        plan.execute(xin, wl.nsamp, out, stream)
+        ev[1].record(stream)
+        c, n = plan.search(out, capacity=1 << 18, stream=stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]), ev[0].elapsed_time(ev[2]), c
+
+    for _ in range(args.warmup):
+        step(sp, out_s)
+        step(bf, out_b)
+    ts, tb = [], []
+    for _ in range(args.steps):
+        ts.append(step(sp, out_s))
+        tb.append(step(bf, out_b))
+    ex_s = statistics.median(t[0] for t in ts)
+    st_s = statistics.median(t[1] for t in ts)
+    ex_b = statistics.median(t[0] for t in tb)
+    st_b = statistics.median(t[1] for t in tb)
+
+    def best_snr(cands, p):
+        i0 = int(round(p.dm / 0.05))
+        sel = cands[(np.abs(cands["dm_idx"] - i0) <= G) & (np.abs(cands["t"] - p.t0) <= 64)]
+        return float(sel["snr"].max()) if len(sel) else 0.0
+
+    snr = [(best_snr(ts[-1][2], p), best_snr(tb[-1][2], p)) for p in pulses]
+    K = sp.n_nominal
+    L = sp.work_bytes // (4 * nsub * K)
+    adds_sub = K * wl.nchans * L + wl.ndm * nsub * sp.nsamp_out
+    adds_bf = wl.ndm * wl.nchans * bf.nsamp_out
+    units = wl.ndm * sp.nsamp_out
+    line = {
+        "mode": "subband", "metric": METRIC, "value": units / (st_s / 1e3), "unit": METRIC,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": st_s,
+        "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "lofar_f32 (1024 ch, 2^20 samples, 2000 DMs 0-99.95) + 16 pulses",
+                   "dms_per_nominal": G, "nsub": nsub, "n_nominal": K, "maxshift": sp.maxshift,
+                   "series_bytes": sp.work_bytes},
+        "subband": {"execute_ms": ex_s, "step_ms": st_s, "adds": adds_sub,
+                    "tadd_s": adds_sub / (ex_s / 1e3) / 1e12},
+        "brute_force": {"execute_ms": ex_b, "step_ms": st_b, "adds": adds_bf,
+                        "tadd_s": adds_bf / (ex_b / 1e3) / 1e12, "tile": bf.tile},
+        "speedup_execute": ex_b / ex_s, "speedup_step": st_b / st_s,
+        "pulse_snr": {"subband": [round(a, 2) for a, _ in snr], "brute_force": [round(b, 2) for _, b in snr],
+                      "mean_ratio": float(np.mean([a / b for a, b in snr if b > 0]))},
+    }
+    sp.close()
+    bf.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="lofar", choices=["lofar", "batch", "serve"],
+    ap.add_argument("--mode", default="lofar", choices=["lofar", "batch", "serve", "subband"],
                     help="lofar: the benchmark line; batch: the 24-beam batched workload; "
-                         "serve: the 64-beam streaming workload")
+                         "serve: the 64-beam streaming workload; subband: Section 3.2 "
+                         "subband de-dispersion of the lofar workload vs brute force")
+    ap.add_argument("--dms-per-nominal", type=int, default=24, help="subband: fine DMs per nominal DM")
+    ap.add_argument("--nsub", type=int, default=32, help="subband: number of subbands")
     ap.add_argument("--speed", type=float, default=4.0, help="serve: arrival rate / real-time rate")
     ap.add_argument("--workers", type=int, default=4, help="serve: server worker streams")
     ap.add_argument("--serve-limit", type=float, default=240.0, help="serve: wall-clock limit (s)")
@@ -562,6 +649,9 @@ def main():
         return
     if args.mode == "serve":
         run_serve(args)
+        return
+    if args.mode == "subband":
+        run_subband(args)
         return
     if world > 1:
         import torch

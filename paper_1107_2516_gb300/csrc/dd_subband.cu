@@ -56,9 +56,10 @@ struct SubLaunch {
     size_t smem;
 };
 
-// Kernel 3's tile shape (16 samples per lane x 8 trials per warp, 4 warps).
-constexpr int kSubTI = 16, kSubDR = 8, kSubNW = 4;
-constexpr int kSubDB = kSubDR * kSubNW;
+// Kernel 3's tile shape: 16 samples per lane x 8 trials per warp; 3 or 4
+// warps per block, chosen per stage so that blocks of 24 or 32 trials leave
+// the fewest trial slots idle (e.g. groups of 24 fine DMs).
+constexpr int kSubTI = 16, kSubDR = 8;
 
 template <typename Tin, bool kInt, bool kStats, int TI, int DR, int NW>
 __global__ void __launch_bounds__(NW * 32, 3) sub_kernel(SubLaunch a)
@@ -209,25 +210,46 @@ __global__ void __launch_bounds__(NW * 32, 3) sub_kernel(SubLaunch a)
 
 // stage 1 (input dtype -> float series) and stage 2 (float series -> out)
 template <typename Tin, bool kInt, bool kStats>
-static cudaError_t sub_launch(const SubLaunch &a, cudaStream_t s)
+static cudaError_t sub_launch(const SubLaunch &a, int nw, cudaStream_t s)
 {
     const unsigned grid = (unsigned)(a.ntile * a.nblk);
-    sub_kernel<Tin, kInt, kStats, kSubTI, kSubDR, kSubNW><<<grid, kSubNW * 32, a.smem, s>>>(a);
+    if (nw == 3)
+        sub_kernel<Tin, kInt, kStats, kSubTI, kSubDR, 3><<<grid, 3 * 32, a.smem, s>>>(a);
+    else
+        sub_kernel<Tin, kInt, kStats, kSubTI, kSubDR, 4><<<grid, 4 * 32, a.smem, s>>>(a);
     return cudaGetLastError();
+}
+
+template <typename Tin, bool kInt, bool kStats>
+static cudaError_t sub_prepare_one(size_t optin)
+{
+    cudaError_t e = allow_max_dynamic_smem((const void *)sub_kernel<Tin, kInt, kStats, kSubTI, kSubDR, 3>, optin);
+    if (e == cudaSuccess)
+        e = allow_max_dynamic_smem((const void *)sub_kernel<Tin, kInt, kStats, kSubTI, kSubDR, 4>, optin);
+    return e;
 }
 
 static cudaError_t sub_prepare(size_t optin)
 {
-    cudaError_t e = allow_max_dynamic_smem((const void *)sub_kernel<float, false, false, kSubTI, kSubDR, kSubNW>, optin);
-    if (e == cudaSuccess) e = allow_max_dynamic_smem((const void *)sub_kernel<__half, false, false, kSubTI, kSubDR, kSubNW>, optin);
-    if (e == cudaSuccess) e = allow_max_dynamic_smem((const void *)sub_kernel<uint8_t, false, false, kSubTI, kSubDR, kSubNW>, optin);
-    if (e == cudaSuccess) e = allow_max_dynamic_smem((const void *)sub_kernel<float, false, true, kSubTI, kSubDR, kSubNW>, optin);
-    if (e == cudaSuccess) e = allow_max_dynamic_smem((const void *)sub_kernel<float, true, true, kSubTI, kSubDR, kSubNW>, optin);
+    cudaError_t e = sub_prepare_one<float, false, false>(optin);
+    if (e == cudaSuccess) e = sub_prepare_one<__half, false, false>(optin);
+    if (e == cudaSuccess) e = sub_prepare_one<uint8_t, false, false>(optin);
+    if (e == cudaSuccess) e = sub_prepare_one<float, false, true>(optin);
+    if (e == cudaSuccess) e = sub_prepare_one<float, true, true>(optin);
     return e;
+}
+
+// Warps per block (3 or 4) for runs of n trials: fewest idle trial slots,
+// ties to 4.
+static int pick_nw(int n)
+{
+    auto idle = [&](int nw) { const int db = kSubDR * nw; return (n + db - 1) / db * db - n; };
+    return idle(3) < idle(4) ? 3 : 4;
 }
 
 // One stage's block list and delay records, host and device.
 struct SubStage {
+    int nw = 4, db = 32;             // warps per block, trials per block
     std::vector<SubBlock> blocks;
     std::vector<int32_t> offs, base;
     SubBlock *d_blocks = nullptr;
@@ -257,7 +279,7 @@ static void add_block(SubStage &st, int in_row, int nc, int row0, int ntr, int a
         for (int j = 0; j < ntr; ++j) { const int d = delay(j, c); lo = std::min(lo, d); hi = std::max(hi, d); }
         const int r0 = lo - (lo % al);
         st.base.push_back(r0);
-        for (int j = 0; j < kSubDB; ++j) st.offs.push_back(delay(std::min(j, ntr - 1), c) - r0);
+        for (int j = 0; j < st.db; ++j) st.offs.push_back(delay(std::min(j, ntr - 1), c) - r0);
         need = std::max<long long>(need, (long long)(hi - r0) + 32LL * kSubTI);
     }
 }
@@ -266,7 +288,7 @@ static int finish_stage(SubStage &st, long long need, size_t eb, size_t optin)
 {
     st.rs = (int)((need + 15) / 16 * 16);
     const size_t budget = std::min<size_t>(optin, (228 * 1024) / 3 - 1024) - 1024;
-    const size_t per_ch = (size_t)st.rs * eb + kSubDB * sizeof(int32_t);
+    const size_t per_ch = (size_t)st.rs * eb + (size_t)st.db * sizeof(int32_t);
     st.ch = (int)std::min<size_t>(16, budget / (kStages * per_ch));
     if (st.ch < 1) return set_error(DD_ERR_ARG, "subband rows too long for shared memory (%d samples)", st.rs);
     st.bar_off = (int)(((size_t)kStages * st.ch * per_ch + 15) / 16 * 16);
@@ -372,12 +394,15 @@ int dd_subband_plan_create(int32_t nchans, double fch1_mhz, double foff_mhz, dou
     f->nsamp_out = p->nsamp_out;
     p->L = (p->nsamp_out + d2max + 3) / 4 * 4;
 
-    // stage 1 blocks: per subband, nominal DMs in chunks of kSubDB
+    // stage 1 blocks: per subband, nominal DMs in chunks of db
     const int al_in = (int)(16 / in_elem_bytes((dd_dtype)in_dtype));
     long long need1 = 0, need2 = 0;
+    p->st1.nw = pick_nw(K); p->st1.db = kSubDR * p->st1.nw;
+    p->st2.nw = pick_nw(G); p->st2.db = kSubDR * p->st2.nw;
+    const int db1 = p->st1.db, db2 = p->st2.db;
     for (int s = 0; s < S; ++s)
-        for (int k0 = 0; k0 < K; k0 += kSubDB) {
-            const int nt = std::min(kSubDB, K - k0);
+        for (int k0 = 0; k0 < K; k0 += db1) {
+            const int nt = std::min(db1, K - k0);
             add_block(p->st1, s * cs, cs, s * K + k0, nt, al_in, need1,
                       [&](int j, int c) { return p->d1[(size_t)(k0 + j) * C + s * cs + c]; });
         }
@@ -385,8 +410,8 @@ int dd_subband_plan_create(int32_t nchans, double fch1_mhz, double foff_mhz, dou
     // group k is series row s*K + k
     for (int k = 0; k < K; ++k) {
         const int j0 = k * G, j1 = std::min(j0 + G, D);
-        for (int jb = j0; jb < j1; jb += kSubDB) {
-            const int nt = std::min(kSubDB, j1 - jb);
+        for (int jb = j0; jb < j1; jb += db2) {
+            const int nt = std::min(db2, j1 - jb);
             add_block(p->st2, k, S, jb, nt, 4, need2,
                       [&](int j, int s) { return p->d2[(size_t)(jb + j) * S + s]; });
         }
@@ -454,9 +479,10 @@ int dd_subband_execute(dd_subband_plan *plan, const void *in_dev, int64_t in_pit
     a.out = plan->d_inter; a.out_pitch = plan->L; a.nout = plan->L;
     a.partials = nullptr; a.err = plan->d_err;
     if (a.ntile * a.nblk > INT32_MAX) return set_error(DD_ERR_ARG, "subband stage 1 grid too large");
-    cudaError_t e = f->dtype == DD_F32 ? sub_launch<float, false, false>(a, s)
-                  : f->dtype == DD_F16 ? sub_launch<__half, false, false>(a, s)
-                                       : sub_launch<uint8_t, false, false>(a, s);
+    const int nw1 = plan->st1.nw, nw2 = plan->st2.nw;
+    cudaError_t e = f->dtype == DD_F32 ? sub_launch<float, false, false>(a, nw1, s)
+                  : f->dtype == DD_F16 ? sub_launch<__half, false, false>(a, nw1, s)
+                                       : sub_launch<uint8_t, false, false>(a, nw1, s);
     if (e != cudaSuccess) return cuda_fail(e, "launch subband stage 1");
 
     // stage 2: series -> out [ndm][nsamp_out], with statistics partials
@@ -473,7 +499,7 @@ int dd_subband_execute(dd_subband_plan *plan, const void *in_dev, int64_t in_pit
     int rc = ensure_partials_public(f, np);
     if (rc) return rc;
     b.partials = f->d_partials;
-    e = f->dtype == DD_U8 ? sub_launch<float, true, true>(b, s) : sub_launch<float, false, true>(b, s);
+    e = f->dtype == DD_U8 ? sub_launch<float, true, true>(b, nw2, s) : sub_launch<float, false, true>(b, nw2, s);
     if (e != cudaSuccess) return cuda_fail(e, "launch subband stage 2");
     f->n_partials = np;
     f->stats_out = out_dev;
