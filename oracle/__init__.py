@@ -13,6 +13,7 @@ Paper passages followed (Magro et al. 2011):
   Section 3.1              brute-force sum           -> dedisperse()
   Section 3 (output thread) mean, sigma, n-sigma test -> stats(), search()
   Section 3.2              subband de-dispersion     -> subband_tables(), subband_dedisperse()
+  Section 3.2, Table 1     binning, survey passes    -> bin_samples(), survey_passes()
 """
 from __future__ import annotations
 
@@ -83,6 +84,10 @@ def _load():
         for name in ("oracle_subband_f32", "oracle_subband_f16", "oracle_subband_u8"):
             getattr(lib, name).restype = None
             getattr(lib, name).argtypes = [vp, i64, i64, i64, vp, vp, i64, i64, i64, vp]
+        lib.oracle_bin.restype = None
+        lib.oracle_bin.argtypes = [vp, C.c_int, i64, i64, i64, i64, vp, i64]
+        lib.oracle_subband_f64.restype = None
+        lib.oracle_subband_f64.argtypes = [vp, i64, i64, i64, vp, vp, i64, i64, i64, vp]
         lib.oracle_subband_point_f32.restype = f64
         lib.oracle_subband_point_f32.argtypes = [vp, i64, i64, i64, vp, vp, i64, i64, i64]
         _lib = lib
@@ -244,7 +249,10 @@ def subband_dedisperse(data: np.ndarray, d1: np.ndarray, d2: np.ndarray, G: int,
         need = max(need, int(e.max()))
     if nout < 0 or (nout > 0 and need + nout > pitch):
         raise ValueError("input too short for nout + maxshift")
-    if data.dtype == np.float32:
+    if data.dtype == np.float64:
+        out = np.empty((ndm, nout), np.float64)
+        lib.oracle_subband_f64(_p(data), pitch, nchans, nsub, _p(d1), _p(d2), G, ndm, nout, _p(out))
+    elif data.dtype == np.float32:
         out = np.empty((ndm, nout), np.float64)
         lib.oracle_subband_f32(_p(data), pitch, nchans, nsub, _p(d1), _p(d2), G, ndm, nout, _p(out))
     elif data.dtype == np.uint16:
@@ -265,3 +273,30 @@ def subband_point_f32(data: np.ndarray, d1: np.ndarray, d2: np.ndarray, G: int, 
     d2 = np.ascontiguousarray(d2, dtype=np.int64)
     return float(_load().oracle_subband_point_f32(_p(data), data.shape[1], data.shape[0],
                                                   d2.shape[1], _p(d1), _p(d2), G, int(j), int(t)))
+
+
+def bin_samples(data: np.ndarray, nb: int, nsamp: int = None) -> np.ndarray:
+    """Binning (Section 3.2): mean of nb adjacent samples per channel, in double.
+
+    data: [nchans][pitch] float32, uint8 or uint16 (binary16 bits); the first
+    nsamp samples (default: all) give floor(nsamp / nb) binned samples."""
+    data = np.ascontiguousarray(data)
+    nchans, pitch = data.shape
+    nsamp = pitch if nsamp is None else int(nsamp)
+    code = {np.dtype(np.float32): 0, np.dtype(np.uint8): 1, np.dtype(np.uint16): 2}[data.dtype]
+    n = nsamp // nb
+    out = np.empty((nchans, max(n, 1)), np.float64)
+    _load().oracle_bin(_p(data), code, pitch, nchans, nsamp, int(nb), _p(out), out.shape[1])
+    return out[:, :n]
+
+
+def survey_passes(passes) -> list:
+    """Reading of a Table 1 survey plan: each pass (low DM, high DM, DM step,
+    bin, subband DM step) gives round((high - low) / step) fine DMs
+    low + i * step and round(subband step / step) fine DMs per nominal DM.
+    Returns [(dm_list, bin, dms_per_nominal)]."""
+    out = []
+    for lo, hi, step, nb, sub in passes:
+        n = int(round((hi - lo) / step))
+        out.append(([lo + i * step for i in range(n)], int(nb), int(round(sub / step))))
+    return out

@@ -494,3 +494,52 @@ ORACLE_API double oracle_subband_point_f32(const float *in, int64_t pitch, int64
 {
     return subband_point(in, NULL, pitch, nchans, nsub, d1, d2, G, j, t);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Section 3.2, binning: average of N_b adjacent samples,                    */
+/*   out[c][i] = (1/N_b) sum_{q<N_b} in[c][N_b*i + q],  i < floor(n / N_b).   */
+/* In double; the subband stages below then run on the binned series.        */
+/* ------------------------------------------------------------------------ */
+static double in_value(const void *in, int dtype, int64_t i)
+{
+    /* dtype: 0 float32, 1 uint8, 2 binary16 (the library's dd_dtype codes) */
+    if (dtype == 0) return (double)((const float *)in)[i];
+    if (dtype == 1) return (double)((const uint8_t *)in)[i];
+    return oracle_half_to_double(((const uint16_t *)in)[i]);
+}
+
+ORACLE_API void oracle_bin(const void *in, int dtype, int64_t pitch, int64_t nchans, int64_t nsamp,
+                           int64_t nb, double *out, int64_t out_pitch)
+{
+    const int64_t n = nsamp / nb;
+    for (int64_t c = 0; c < nchans; ++c)
+        for (int64_t i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int64_t q = 0; q < nb; ++q)
+                s += in_value(in, dtype, c * pitch + i * nb + q);
+            out[c * out_pitch + i] = s / (double)nb;
+        }
+}
+
+/* Subband stages on double input (binned series), as oracle_subband_f32. */
+ORACLE_API void oracle_subband_f64(const double *in, int64_t pitch, int64_t nchans, int64_t nsub,
+                                   const int64_t *d1, const int64_t *d2, int64_t G, int64_t ndm,
+                                   int64_t nout, double *out)
+{
+    const int64_t cs = nchans / nsub;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t j = 0; j < ndm; ++j) {
+        const int64_t *r1 = d1 + (j / G) * nchans;
+        for (int64_t t = 0; t < nout; ++t) {
+            double acc = 0.0;
+            for (int64_t s = 0; s < nsub; ++s) {
+                const int64_t tt = t + d2[j * nsub + s];
+                double sub = 0.0;
+                for (int64_t c = s * cs; c < (s + 1) * cs; ++c)
+                    sub += in[c * pitch + tt + r1[c]];
+                acc += sub;
+            }
+            out[j * nout + t] = acc;
+        }
+    }
+}
