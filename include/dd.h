@@ -384,6 +384,55 @@ DD_API int dd_subband_search(dd_subband_plan *plan, const void *out_dev, dd_cand
 /* mu and sigma used by the last dd_subband_search. */
 DD_API int dd_subband_last_stats(const dd_subband_plan *plan, double *mu, double *sigma);
 
+/* ---------------------------------------------------------------------
+ * Survey plans (Section 3.2 with binning; the plans of Table 1 / Table 4):
+ * several passes over disjoint DM ranges, each binning the input by its
+ * factor and running subband de-dispersion at the binned sampling time.
+ *
+ * A pass is one row of the paper's survey-plan table: fine DM trials
+ * low_dm + i*dm_step for i < round((high_dm - low_dm) / dm_step), input
+ * binned by `bin` (average of `bin` adjacent samples: x_b[c][i] =
+ * (1/bin) sum_{q<bin} x[c][i*bin + q], i < nsamp_in/bin, float32), and
+ * round(sub_dm_step / dm_step) fine DMs per nominal DM.  Each pass is a
+ * dd_subband_plan with tsamp_s*bin, nsamp_in/bin samples and nsub subbands
+ * (input dtype for bin 1, float32 otherwise).  Pass outputs are
+ * [ndm][nsamp_out] at the pass's resolution, caller-owned.  The plan owns
+ * the binned inputs (nchans x nsamp_in/bin float32 per pass with bin > 1)
+ * and each pass's subband series.  Arguments as dd_subband_plan_create. */
+typedef struct {
+    double low_dm, high_dm, dm_step;   /* pc cm^-3 */
+    int32_t bin;                       /* binning factor N_b >= 1 */
+    int32_t reserved;
+    double sub_dm_step;                /* DM step between nominal DMs */
+} dd_survey_pass;
+
+typedef struct dd_survey_plan dd_survey_plan;
+
+DD_API int dd_survey_plan_create(int32_t nchans, double fch1_mhz, double foff_mhz, double tsamp_s,
+                                 const dd_survey_pass *passes, int32_t npass, int32_t nsub,
+                                 const int32_t *boxcar_widths, int32_t nwidths, double sigma,
+                                 int32_t in_dtype, int64_t nsamp_in, dd_survey_plan **plan_out);
+
+/* Synchronises the device, then frees everything the plan owns. */
+DD_API int dd_survey_plan_destroy(dd_survey_plan *plan);
+
+/* Geometry of pass `pass` (any pointer may be NULL; dm_list: [ndm] host). */
+DD_API int dd_survey_pass_info(const dd_survey_plan *plan, int32_t pass, int32_t *ndm, int32_t *bin,
+                               int32_t *dms_per_nominal, int64_t *maxshift, int64_t *nsamp_out,
+                               double *dm_list);
+
+/* Every pass, asynchronously on `stream`: in_dev [nchans][in_pitch] (16-byte
+ * aligned rows), out_devs[npass] device buffers of [ndm][nsamp_out]. */
+DD_API int dd_survey_execute(dd_survey_plan *plan, const void *in_dev, int64_t in_pitch,
+                             void *const *out_devs, void *stream);
+
+/* Search of one pass's output (dd_subband_search; its own mu/sigma). */
+DD_API int dd_survey_search(dd_survey_plan *plan, int32_t pass, const void *out_dev,
+                            dd_candidate *cand_host, int64_t capacity, int64_t *n_found, void *stream);
+
+/* mu and sigma used by the last dd_survey_search of pass `pass`. */
+DD_API int dd_survey_last_stats(const dd_survey_plan *plan, int32_t pass, double *mu, double *sigma);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 DD_API const char *dd_last_error(void);
 

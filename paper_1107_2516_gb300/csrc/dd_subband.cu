@@ -529,3 +529,168 @@ int dd_subband_last_stats(const dd_subband_plan *plan, double *mu, double *sigma
 }
 
 }  // extern "C"
+
+// ===================================================================== survey
+// Multi-pass survey plans (Section 3.2 with binning; the plans of Table 1 /
+// Table 4): each pass bins the input by its factor N_b (average of N_b
+// adjacent samples) and runs subband de-dispersion over its DM range at the
+// binned sampling time.
+
+namespace dd {
+
+// out[c][i] = (1/nb) * sum_{q<nb} in[c][i*nb + q], float32 result.  Thread i
+// of a row reads nb consecutive samples: a warp covers 32*nb consecutive
+// inputs, so the reads are coalesced for any nb.
+template <typename Tin>
+__global__ void bin_kernel(const Tin *__restrict__ in, int64_t pitch, int64_t nbin, int nb,
+                           float *__restrict__ out, int64_t out_pitch)
+{
+    const int64_t c = blockIdx.y;
+    const float inv = 1.0f / (float)nb;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nbin;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const Tin *p = in + c * pitch + i * nb;
+        float s = 0.f;
+        for (int q = 0; q < nb; ++q) s += lane_ld<Tin>(p + q);
+        out[c * out_pitch + i] = nb == 1 ? s : s * inv;
+    }
+}
+
+}  // namespace dd
+
+struct dd_survey_plan {
+    int nchans = 0;
+    dd_dtype dtype = DD_F32;
+    int64_t nsamp_in = 0;
+    std::vector<dd_subband_plan *> sub;   // one per pass
+    std::vector<int> bin;
+    std::vector<float *> d_bin;            // binned input per pass (bin > 1)
+    std::vector<int64_t> bin_n, bin_pitch;
+};
+
+static void free_survey(dd_survey_plan *p)
+{
+    if (!p) return;
+    for (auto *s : p->sub) free_subband(s);
+    for (auto *b : p->d_bin) if (b) cudaFree(b);
+    delete p;
+}
+
+extern "C" {
+
+int dd_survey_plan_create(int32_t nchans, double fch1_mhz, double foff_mhz, double tsamp_s,
+                          const dd_survey_pass *passes, int32_t npass, int32_t nsub,
+                          const int32_t *boxcar_widths, int32_t nwidths, double sigma,
+                          int32_t in_dtype, int64_t nsamp_in, dd_survey_plan **plan_out)
+{
+    if (!plan_out) return set_error(DD_ERR_ARG, "plan_out is NULL");
+    *plan_out = nullptr;
+    if (!passes || npass < 1) return set_error(DD_ERR_ARG, "need npass >= 1 passes");
+    dd_survey_plan *p = new (std::nothrow) dd_survey_plan();
+    if (!p) return set_error(DD_ERR_NOMEM, "host allocation failed");
+    p->nchans = nchans; p->dtype = (dd_dtype)in_dtype; p->nsamp_in = nsamp_in;
+    for (int i = 0; i < npass; ++i) {
+        const dd_survey_pass &ps = passes[i];
+        if (!(ps.dm_step > 0.0) || !(ps.high_dm > ps.low_dm) || ps.bin < 1 || !(ps.sub_dm_step > 0.0)) {
+            free_survey(p);
+            return set_error(DD_ERR_ARG, "pass %d: need dm_step > 0, high_dm > low_dm, bin >= 1, sub_dm_step > 0", i);
+        }
+        const long long ndm = llround((ps.high_dm - ps.low_dm) / ps.dm_step);
+        const long long G = llround(ps.sub_dm_step / ps.dm_step);
+        if (ndm < 1 || ndm > INT32_MAX || G < 1) {
+            free_survey(p);
+            return set_error(DD_ERR_ARG, "pass %d: fewer than one DM trial or trial per nominal DM", i);
+        }
+        std::vector<double> dms((size_t)ndm);
+        for (long long j = 0; j < ndm; ++j) dms[(size_t)j] = ps.low_dm + (double)j * ps.dm_step;
+        const int64_t nb = nsamp_in / ps.bin;
+        dd_subband_plan *sp = nullptr;
+        const int rc = dd_subband_plan_create(nchans, fch1_mhz, foff_mhz, tsamp_s * (double)ps.bin, dms.data(),
+                                              (int32_t)ndm, (int32_t)G, nsub, boxcar_widths, nwidths, sigma,
+                                              ps.bin == 1 ? in_dtype : (int32_t)DD_F32, nb, &sp);
+        if (rc) { free_survey(p); return rc; }
+        p->sub.push_back(sp);
+        p->bin.push_back(ps.bin);
+        p->d_bin.push_back(nullptr);
+        p->bin_n.push_back(nb);
+        p->bin_pitch.push_back((nb + 3) / 4 * 4);
+    }
+    *plan_out = p;
+    return DD_OK;
+}
+
+int dd_survey_plan_destroy(dd_survey_plan *plan)
+{
+    if (!plan) return DD_OK;
+    cudaDeviceSynchronize();
+    free_survey(plan);
+    return DD_OK;
+}
+
+int dd_survey_pass_info(const dd_survey_plan *plan, int32_t pass, int32_t *ndm, int32_t *bin,
+                        int32_t *dms_per_nominal, int64_t *maxshift, int64_t *nsamp_out, double *dm_list)
+{
+    if (!plan) return set_error(DD_ERR_ARG, "plan is NULL");
+    if (pass < 0 || pass >= (int)plan->sub.size()) return set_error(DD_ERR_ARG, "no pass %d", pass);
+    const dd_subband_plan *sp = plan->sub[pass];
+    if (ndm) *ndm = sp->fine->ndm;
+    if (bin) *bin = plan->bin[pass];
+    if (dms_per_nominal) *dms_per_nominal = sp->G;
+    if (maxshift) *maxshift = sp->maxshift;
+    if (nsamp_out) *nsamp_out = sp->nsamp_out;
+    if (dm_list) memcpy(dm_list, sp->fine->dm_list.data(), sp->fine->dm_list.size() * sizeof(double));
+    return DD_OK;
+}
+
+int dd_survey_execute(dd_survey_plan *plan, const void *in_dev, int64_t in_pitch, void *const *out_devs,
+                      void *stream)
+{
+    if (!plan) return set_error(DD_ERR_ARG, "plan is NULL");
+    if (!in_dev || !out_devs) return set_error(DD_ERR_ARG, "NULL buffer");
+    if (in_pitch < plan->nsamp_in) return set_error(DD_ERR_ARG, "in_pitch < nsamp_in");
+    cudaStream_t s = (cudaStream_t)stream;
+    for (size_t i = 0; i < plan->sub.size(); ++i) {
+        if (!out_devs[i]) return set_error(DD_ERR_ARG, "out_devs[%d] is NULL", (int)i);
+        const void *src = in_dev;
+        int64_t pitch = in_pitch;
+        const int nb = plan->bin[i];
+        if (nb > 1) {
+            if (!plan->d_bin[i]) {
+                cudaError_t e = cudaMalloc(&plan->d_bin[i], (size_t)plan->nchans * plan->bin_pitch[i] * sizeof(float));
+                if (e != cudaSuccess) { plan->d_bin[i] = nullptr; return cuda_fail(e, "cudaMalloc(binned input)"); }
+            }
+            const int64_t n = plan->bin_n[i];
+            const dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 4096), (unsigned)plan->nchans);
+            if (plan->dtype == DD_F32)
+                bin_kernel<float><<<grid, 256, 0, s>>>((const float *)in_dev, in_pitch, n, nb, plan->d_bin[i], plan->bin_pitch[i]);
+            else if (plan->dtype == DD_F16)
+                bin_kernel<__half><<<grid, 256, 0, s>>>((const __half *)in_dev, in_pitch, n, nb, plan->d_bin[i], plan->bin_pitch[i]);
+            else
+                bin_kernel<uint8_t><<<grid, 256, 0, s>>>((const uint8_t *)in_dev, in_pitch, n, nb, plan->d_bin[i], plan->bin_pitch[i]);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "launch bin_kernel");
+            src = plan->d_bin[i];
+            pitch = plan->bin_pitch[i];
+        }
+        const int rc = dd_subband_execute(plan->sub[i], src, pitch, out_devs[i], stream);
+        if (rc) return rc;
+    }
+    return DD_OK;
+}
+
+int dd_survey_search(dd_survey_plan *plan, int32_t pass, const void *out_dev, dd_candidate *cand_host,
+                     int64_t capacity, int64_t *n_found, void *stream)
+{
+    if (!plan) return set_error(DD_ERR_ARG, "plan is NULL");
+    if (pass < 0 || pass >= (int)plan->sub.size()) return set_error(DD_ERR_ARG, "no pass %d", pass);
+    return dd_subband_search(plan->sub[pass], out_dev, cand_host, capacity, n_found, stream);
+}
+
+int dd_survey_last_stats(const dd_survey_plan *plan, int32_t pass, double *mu, double *sigma)
+{
+    if (!plan) return set_error(DD_ERR_ARG, "plan is NULL");
+    if (pass < 0 || pass >= (int)plan->sub.size()) return set_error(DD_ERR_ARG, "no pass %d", pass);
+    return dd_subband_last_stats(plan->sub[pass], mu, sigma);
+}
+
+}  // extern "C"

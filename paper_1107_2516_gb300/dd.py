@@ -34,7 +34,9 @@ EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "d
            "dd_server_create", "dd_server_destroy", "dd_server_add_beam", "dd_server_remove_beam",
            "dd_server_submit", "dd_server_poll", "dd_server_candidates", "dd_server_beam_info",
            "dd_server_memory", "dd_subband_plan_create", "dd_subband_plan_destroy",
-           "dd_subband_plan_info", "dd_subband_execute", "dd_subband_search", "dd_subband_last_stats")
+           "dd_subband_plan_info", "dd_subband_execute", "dd_subband_search", "dd_subband_last_stats",
+           "dd_survey_plan_create", "dd_survey_plan_destroy", "dd_survey_pass_info", "dd_survey_execute",
+           "dd_survey_search", "dd_survey_last_stats")
 
 DD_PRIMING = 7
 
@@ -109,6 +111,14 @@ def load(path: Optional[str] = None):
             "dd_subband_execute": (C.c_int, [vp, vp, i64, vp, vp]),
             "dd_subband_search": (C.c_int, [vp, vp, vp, i64, P64, vp]),
             "dd_subband_last_stats": (C.c_int, [vp, C.POINTER(f64), C.POINTER(f64)]),
+            "dd_survey_plan_create": (C.c_int, [i32, f64, f64, f64, vp, i32, i32, vp, i32, f64, i32, i64,
+                                                C.POINTER(vp)]),
+            "dd_survey_plan_destroy": (C.c_int, [vp]),
+            "dd_survey_pass_info": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32), P64,
+                                              P64, vp]),
+            "dd_survey_execute": (C.c_int, [vp, vp, i64, vp, vp]),
+            "dd_survey_search": (C.c_int, [vp, i32, vp, vp, i64, P64, vp]),
+            "dd_survey_last_stats": (C.c_int, [vp, i32, C.POINTER(f64), C.POINTER(f64)]),
             "dd_last_error": (C.c_char_p, []),
             "dd_version": (C.c_char_p, []),
         }
@@ -555,6 +565,103 @@ class SubbandPlan:
     def close(self):
         if self.handle:
             dd_subband_plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ survey plans (Table 1)
+
+class SurveyPass(C.Structure):
+    """One row of a survey plan (Table 1): DM range, DM step, binning factor,
+    subband DM step."""
+    _fields_ = [("low_dm", C.c_double), ("high_dm", C.c_double), ("dm_step", C.c_double),
+                ("bin", C.c_int32), ("reserved", C.c_int32), ("sub_dm_step", C.c_double)]
+
+
+def dd_survey_plan_create(nchans, fch1, foff, tsamp, passes, nsub, boxcar_widths, sigma, in_dtype,
+                          nsamp_in) -> int:
+    arr = (SurveyPass * len(passes))(*[SurveyPass(float(lo), float(hi), float(st), int(b), 0, float(sub))
+                                       for lo, hi, st, b, sub in passes])
+    w = np.ascontiguousarray(np.asarray(boxcar_widths, dtype=np.int32))
+    out = C.c_void_p()
+    _check(load().dd_survey_plan_create(int(nchans), float(fch1), float(foff), float(tsamp), C.cast(arr, C.c_void_p),
+                                        len(passes), int(nsub), w.ctypes.data, int(w.size), float(sigma),
+                                        int(in_dtype), int(nsamp_in), C.byref(out)))
+    return int(out.value)
+
+
+def dd_survey_plan_destroy(plan: int) -> None:
+    _check(load().dd_survey_plan_destroy(plan))
+
+
+def dd_survey_pass_info(plan: int, pass_idx: int, dm_list=False):
+    """(ndm, bin, dms_per_nominal, maxshift, nsamp_out[, dm_list])."""
+    nd, b, g = C.c_int32(), C.c_int32(), C.c_int32()
+    m, n = C.c_int64(), C.c_int64()
+    lib = load()
+    _check(lib.dd_survey_pass_info(plan, int(pass_idx), C.byref(nd), C.byref(b), C.byref(g), C.byref(m),
+                                   C.byref(n), None))
+    base = (int(nd.value), int(b.value), int(g.value), int(m.value), int(n.value))
+    if not dm_list:
+        return base
+    dms = np.empty(base[0], np.float64)
+    _check(lib.dd_survey_pass_info(plan, int(pass_idx), None, None, None, None, None, _ptr(dms)))
+    return base + (dms,)
+
+
+def dd_survey_execute(plan: int, in_dev, in_pitch: int, out_devs, stream=None) -> None:
+    ptrs = (C.c_void_p * len(out_devs))(*[_ptr(o) for o in out_devs])
+    _check(load().dd_survey_execute(plan, _ptr(in_dev), int(in_pitch), C.cast(ptrs, C.c_void_p),
+                                    _stream(stream)))
+
+
+def dd_survey_search(plan: int, pass_idx: int, out_dev, capacity: int = 1 << 16, stream=None,
+                     allow_overflow=False):
+    cands = np.zeros(max(capacity, 1), dtype=CANDIDATE_DTYPE)
+    n = C.c_int64()
+    _check(load().dd_survey_search(plan, int(pass_idx), _ptr(out_dev), cands.ctypes.data, int(capacity),
+                                   C.byref(n), _stream(stream)),
+           allow=(DD_ERR_OVERFLOW,) if allow_overflow else ())
+    total = int(n.value)
+    return cands[:min(total, capacity)].copy(), total
+
+
+def dd_survey_last_stats(plan: int, pass_idx: int):
+    mu, sg = C.c_double(), C.c_double()
+    _check(load().dd_survey_last_stats(plan, int(pass_idx), C.byref(mu), C.byref(sg)))
+    return float(mu.value), float(sg.value)
+
+
+class SurveyPlan:
+    """Owning wrapper around a dd_survey_plan handle (marshalling only).
+    passes: rows (low_dm, high_dm, dm_step, bin, sub_dm_step)."""
+
+    def __init__(self, nchans, fch1, foff, tsamp, passes, nsub, boxcar_widths, sigma, in_dtype, nsamp_in):
+        self.npass = len(passes)
+        self.handle = dd_survey_plan_create(nchans, fch1, foff, tsamp, passes, nsub, boxcar_widths, sigma,
+                                            in_dtype, nsamp_in)
+        self.passes = [dd_survey_pass_info(self.handle, i) for i in range(self.npass)]
+
+    def dm_list(self, i):
+        return dd_survey_pass_info(self.handle, i, dm_list=True)[5]
+
+    def execute(self, in_dev, in_pitch, out_devs, stream=None):
+        dd_survey_execute(self.handle, in_dev, in_pitch, out_devs, stream)
+
+    def search(self, i, out_dev, capacity=1 << 16, stream=None, allow_overflow=False):
+        return dd_survey_search(self.handle, i, out_dev, capacity, stream, allow_overflow)
+
+    def stats(self, i):
+        return dd_survey_last_stats(self.handle, i)
+
+    def close(self):
+        if self.handle:
+            dd_survey_plan_destroy(self.handle)
             self.handle = 0
 
     def __del__(self):

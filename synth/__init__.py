@@ -61,7 +61,17 @@ WORKLOADS = {
     "lofar_f32": Workload("lofar_f32", nchans=1024, fch1=150.0, foff=-0.01171875,
                           tsamp=163.84e-6, nsamp=1 << 20, ndm=2000, dm_step=0.05,
                           widths=(1, 2, 4, 8, 16, 32), seed=2),
+    # the survey-plan comparison's beam (Table 4: 60 s at 300 MHz, 16 MHz in
+    # 1024 channels); the sampling time is not stated, 64 us is taken.  Its
+    # DM trials come from SURVEY_PLAN (3102 over three passes), not dm_list.
+    "survey_f32": Workload("survey_f32", nchans=1024, fch1=308.0 - 0.0078125, foff=-0.015625,
+                           tsamp=64e-6, nsamp=937500, ndm=3102, dm_step=0.03,
+                           widths=(1, 2, 4, 8, 16, 32), seed=6),
 }
+
+# The survey plan of Table 1 / Table 4: (low DM, high DM, DM step, bin,
+# subband DM step) per pass.
+SURVEY_PLAN = ((0.00, 53.46, 0.03, 1, 0.66), (53.46, 88.26, 0.05, 2, 1.2), (88.26, 150.66, 0.10, 4, 2.4))
 
 
 def workload(name: str) -> Workload:
