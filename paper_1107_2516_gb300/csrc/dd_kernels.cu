@@ -349,6 +349,117 @@ search_kernel(const void *__restrict__ out_, int64_t nout,
     }
 }
 
+// The same search for the common width set {1, 2, 4, ..., 2^(K-1)}.  The
+// tile is staged with kSearchPer independent loads per thread; each thread
+// then copies its kSearchPer samples plus the 2^(K-1) - 1 that follow into
+// registers and forms the boxcars as a doubling tree, B_2w(i) = B_w(i) +
+// B_w(i + w): one add per sample and width, no shared-memory traffic in the
+// loop (the sliding form needs two shared words per sample and width).
+// Integer data stay in int32 (at most 65536 channels x 255 x 64 < 2^31).
+template <bool kInt, int K>
+__global__ void __launch_bounds__(kSearchThreads)
+search_pow2_kernel(const void *__restrict__ out_, int64_t nout, const int32_t *__restrict__ wsorted,
+                   const SearchParams *__restrict__ prm, dd_candidate *__restrict__ cands,
+                   int64_t cap, unsigned long long *__restrict__ count)
+{
+    using T = typename std::conditional<kInt, int32_t, float>::type;
+    constexpr int W = 1 << (K - 1);                 // widest boxcar
+    constexpr int kWin = kSearchPer + W - 1;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    __shared__ int sidx[K];
+    __shared__ float thf[K];
+    __shared__ long long thi[K];
+    T *x = reinterpret_cast<T *>(sraw);
+    const int row = blockIdx.y;
+    const int64_t t0 = (int64_t)blockIdx.x * kSearchTile;
+    if (threadIdx.x < K) {
+        const int o = wsorted[K + threadIdx.x];     // original index of sorted width 2^threadIdx.x
+        sidx[threadIdx.x] = o;
+        thf[threadIdx.x] = prm->thr_f[o];
+        thi[threadIdx.x] = prm->thr_i[o];
+    }
+    const T *src = reinterpret_cast<const T *>(out_) + (size_t)row * nout + t0;
+    const int64_t avail = nout - t0;                // > 0
+    T r[kSearchPer];
+#pragma unroll
+    for (int q = 0; q < kSearchPer; ++q) {
+        const int i = q * kSearchThreads + threadIdx.x;
+        r[q] = i < avail ? src[i] : (T)0;
+    }
+#pragma unroll
+    for (int q = 0; q < kSearchPer; ++q) x[spad(q * kSearchThreads + threadIdx.x)] = r[q];
+    if (threadIdx.x < W - 1) {
+        const int i = kSearchTile + threadIdx.x;
+        x[spad(i)] = i < avail ? src[i] : (T)0;
+    }
+    __syncthreads();
+    const int base = threadIdx.x * kSearchPer;
+    if (base >= avail) return;
+    const int64_t rem = avail - base;               // samples from this thread's first one on
+    T b[kWin];
+#pragma unroll
+    for (int k = 0; k < kWin; ++k) b[k] = x[spad(base + k)];
+#pragma unroll
+    for (int p = 0; p < K; ++p) {
+        const int w = 1 << p;
+        if (p > 0) {
+            // b[k] = B_{w/2}(k) -> B_w(k); ascending k reads b[k + w/2] before it changes
+#pragma unroll
+            for (int k = 0; k + w <= kWin; ++k) b[k] = b[k] + b[k + w / 2];
+        }
+        const int lim = (int)min((int64_t)kSearchPer, rem - w + 1);
+#pragma unroll
+        for (int i = 0; i < kSearchPer; ++i) {
+            bool hit;
+            if constexpr (kInt) hit = (long long)b[i] > thi[p];
+            else hit = b[i] > thf[p];
+            if (hit && i < lim) {
+                const unsigned long long pos = atomicAdd(count, 1ull);
+                if ((int64_t)pos < cap) {
+                    dd_candidate c;
+                    c.dm_idx = row; c.width_idx = sidx[p]; c.t = t0 + base + i;
+                    c.snr = 0.f; c.reserved = 0.f; c.value = (double)b[i];
+                    cands[pos] = c;
+                }
+            }
+        }
+    }
+}
+
+template <bool kInt, int K>
+static void launch_search_pow2(dim3 grid, cudaStream_t s, const void *out, const dd_plan *p)
+{
+    const size_t smem = (size_t)(spad(kSearchTile + (1 << (K - 1)) - 1) + 1) * 4;
+    search_pow2_kernel<kInt, K><<<grid, kSearchThreads, smem, s>>>(out, p->nsamp_out, p->d_wsorted,
+                                                                    p->d_params, p->d_cands, p->cand_cap,
+                                                                    p->d_count);
+}
+
+// K if the plan's widths are exactly {1, 2, ..., 2^(K-1)} with K <= 7, else 0.
+static int pow2_widths(const dd_plan *p)
+{
+    std::vector<int> w(p->widths.begin(), p->widths.end());
+    std::sort(w.begin(), w.end());
+    if (w.size() > 7) return 0;
+    for (size_t i = 0; i < w.size(); ++i)
+        if (w[i] != (1 << i)) return 0;
+    return (int)w.size();
+}
+
+template <bool kInt>
+static void launch_search_pow2_k(int K, dim3 grid, cudaStream_t s, const void *out, const dd_plan *p)
+{
+    switch (K) {
+    case 1: launch_search_pow2<kInt, 1>(grid, s, out, p); break;
+    case 2: launch_search_pow2<kInt, 2>(grid, s, out, p); break;
+    case 3: launch_search_pow2<kInt, 3>(grid, s, out, p); break;
+    case 4: launch_search_pow2<kInt, 4>(grid, s, out, p); break;
+    case 5: launch_search_pow2<kInt, 5>(grid, s, out, p); break;
+    case 6: launch_search_pow2<kInt, 6>(grid, s, out, p); break;
+    default: launch_search_pow2<kInt, 7>(grid, s, out, p); break;
+    }
+}
+
 // S/N of the compacted hits: (B_w - w*mu) / (sigma*sqrt(w)), in double.
 __global__ void cand_snr_kernel(dd_candidate *__restrict__ cands, const unsigned long long *__restrict__ count,
                                 int64_t cap, const int32_t *__restrict__ widths, const SearchParams *__restrict__ prm)
@@ -526,7 +637,11 @@ int search_launch(dd_plan *p, const void *out, cudaStream_t s)
     const int64_t ntile = (p->nsamp_out + kSearchTile - 1) / kSearchTile;
     dim3 grid((unsigned)ntile, (unsigned)p->ndm);
     const size_t smem = (size_t)(spad(kSearchTile + wmax - 1) + 1) * 4;
-    if (isint)
+    const int K = pow2_widths(p);
+    if (K) {
+        if (isint) launch_search_pow2_k<true>(K, grid, s, out, p);
+        else launch_search_pow2_k<false>(K, grid, s, out, p);
+    } else if (isint)
         search_kernel<true><<<grid, kSearchThreads, smem, s>>>(out, p->nsamp_out, p->d_wsorted, p->nwidths,
                                                                wmax, p->d_params, p->d_cands, p->cand_cap, p->d_count);
     else
