@@ -399,6 +399,9 @@ search_pow2_kernel(const void *__restrict__ out_, int64_t nout, const int32_t *_
     T b[kWin];
 #pragma unroll
     for (int k = 0; k < kWin; ++k) b[k] = x[spad(base + k)];
+    // hits as bits p*16 + i (width 2^p, sample i): the unrolled loop stays
+    // compact; the rare appends run once below
+    unsigned long long hits[2] = {0ull, 0ull};
 #pragma unroll
     for (int p = 0; p < K; ++p) {
         const int w = 1 << p;
@@ -407,20 +410,36 @@ search_pow2_kernel(const void *__restrict__ out_, int64_t nout, const int32_t *_
 #pragma unroll
             for (int k = 0; k + w <= kWin; ++k) b[k] = b[k] + b[k + w / 2];
         }
-        const int lim = (int)min((int64_t)kSearchPer, rem - w + 1);
+        unsigned m = 0;
 #pragma unroll
         for (int i = 0; i < kSearchPer; ++i) {
             bool hit;
             if constexpr (kInt) hit = (long long)b[i] > thi[p];
             else hit = b[i] > thf[p];
-            if (hit && i < lim) {
-                const unsigned long long pos = atomicAdd(count, 1ull);
-                if ((int64_t)pos < cap) {
-                    dd_candidate c;
-                    c.dm_idx = row; c.width_idx = sidx[p]; c.t = t0 + base + i;
-                    c.snr = 0.f; c.reserved = 0.f; c.value = (double)b[i];
-                    cands[pos] = c;
-                }
+            m |= (unsigned)hit << i;
+        }
+        const int64_t lim = rem - w + 1;            // tests with t + w <= nout
+        if (lim < kSearchPer) m &= lim > 0 ? (1u << lim) - 1u : 0u;
+        hits[p >> 2] |= (unsigned long long)m << (16 * (p & 3));
+    }
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        unsigned long long bits = hits[h];
+        while (bits) {
+            const int bit = __ffsll((long long)bits) - 1;
+            bits &= bits - 1;
+            const int p = 4 * h + (bit >> 4), i = bit & 15, w = 1 << p;
+            // B_w(i) again, by the same pairwise tree (bit-identical value)
+            T v[1 << (K - 1)];
+            for (int q = 0; q < w; ++q) v[q] = x[spad(base + i + q)];
+            for (int d = 1; d < w; d *= 2)
+                for (int q = 0; q + d < w; q += 2 * d) v[q] = v[q] + v[q + d];
+            const unsigned long long pos = atomicAdd(count, 1ull);
+            if ((int64_t)pos < cap) {
+                dd_candidate c;
+                c.dm_idx = row; c.width_idx = sidx[p]; c.t = t0 + base + i;
+                c.snr = 0.f; c.reserved = 0.f; c.value = (double)v[0];
+                cands[pos] = c;
             }
         }
     }
