@@ -155,7 +155,10 @@ DD_API int dd_process_host(dd_plan *plan, const void *in_host, int64_t in_pitch,
                     dd_candidate *cand_host, int64_t capacity, int64_t *n_found,
                     void *stream);
 
-/* Select the de-dispersion kernel for a plan: 0 = automatic (default),
+/* Select the de-dispersion kernel for a plan: 0 = automatic (default: the
+ * first available of tile configurations 5, 3, 6, 4, 1, 0, 2 — kernel 3
+ * shapes before kernel 2 shapes, in the order of measured speed — or the
+ * autotuner's choice; kernel 1 if no tiled configuration fits),
  * 1 = generic shared-memory kernel, 2 = register-blocked kernel (window
  * reused across 4 DM trials per thread), 3 = lane-interleaved kernel (one
  * conflict-free shared load per add, no branches), 4 = tensor-memory window
@@ -241,8 +244,16 @@ DD_API int dd_batch_autotune(dd_batch *batch, const void *const *in_devs, const 
                              void *const *out_devs, void *stream);
 
 /* Tile configuration the persistent launch uses (-1 if no beam uses it),
- * number of work items, and number of beams run by their own launch. */
+ * number of work items, and number of beams run by their own launch.  A new
+ * batch starts with the first of configurations 5, 3, 6, 4, 1, 0, 2 (kernel
+ * 3 shapes before kernel 2 shapes, see dd_plan_set_tile) that every tiled
+ * beam can use. */
 DD_API int dd_batch_info(const dd_batch *batch, int32_t *config, int64_t *nitems, int32_t *n_separate);
+
+/* Choose the persistent launch's tile configuration (0-6, dd_plan_set_tile's
+ * kernel 2 and kernel 3 shapes); beams that cannot use it run by their own
+ * launch.  Drops a captured graph.  DD_ERR_ARG for another index. */
+DD_API int dd_batch_set_config(dd_batch *batch, int32_t config);
 
 /* ---------------------------------------------------------------------
  * Streaming server.  The paper processes an unbounded stream buffer by

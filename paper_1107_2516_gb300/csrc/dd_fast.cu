@@ -371,9 +371,12 @@ int fast_configure(dd_plan *p)
     p->fast = f;
     if (rc == DD_OK && e != cudaSuccess) rc = cuda_fail(e, "kernel 2 setup");
     if (rc != DD_OK) { fast_release(p); return rc; }
-    for (int k = 0; k < kNumFastCfg; ++k)
-        if (f->cfg[k].ok) { f->active = k; break; }
-    if (f->active < 0) { fast_release(p); return DD_OK; }   // kernel 2 unavailable
+    // default: the first available configuration in the order of measured
+    // speed (kernel 3 shapes, then kernel 2); the autotuner may change it
+    static const int pref[] = {kNumFastCfg + 2, kNumFastCfg + 0, kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
+    for (int k : pref)
+        if (cfg_ok(f, k)) { f->active = k; break; }
+    if (f->active < 0) { fast_release(p); return DD_OK; }   // tiled kernels unavailable
     std::lock_guard<std::mutex> g(g_tune_mu);
     auto it = g_tune_cache.find(tune_key(p));
     if (it != g_tune_cache.end() && cfg_ok(f, it->second.first)) {
@@ -588,6 +591,7 @@ struct dd_batch {
     uint2 *d_items = nullptr;
     int nitems = 0;
     dd::FastLaunch *d_beams = nullptr, *h_beams = nullptr;   // h_beams pinned (graph-capturable copy)
+    dd::LaneLaunch *d_lbeams = nullptr, *h_lbeams = nullptr; // the same for kernel 3 configurations
     unsigned int *d_counter = nullptr;
     int *d_err = nullptr;
     int bar_off = 0;
@@ -601,6 +605,29 @@ namespace dd {
 
 static FastPlan *fp(const dd_plan *p) { return static_cast<FastPlan *>(p->fast); }
 
+// Geometry of configuration k (kernel 2 or kernel 3) of a plan's tables.
+struct BatchGeom { bool ok; int tile, nblk, bar_off; };
+static BatchGeom batch_geom(const FastPlan *f, int k)
+{
+    if (!f || k < 0 || k >= kLaneEnd) return {false, 0, 0, 0};
+    if (k < kNumFastCfg) {
+        const FastCfgData &c = f->cfg[k];
+        return {c.ok, 32 * c.tr, c.nblk, c.bar_off};
+    }
+    const LaneCfgData &c = f->lane[k - kNumFastCfg];
+    return {c.ok, 32 * c.ti, c.nblk, c.bar_off};
+}
+
+static cudaError_t batch_launch_lane(int k, const LaneBatchLaunch &b, int sms, size_t smem, cudaStream_t s)
+{
+    switch (k) {
+    case 0: return lane_batch_launch_c0(b, sms, smem, s);
+    case 1: return lane_batch_launch_c1(b, sms, smem, s);
+    case 2: return lane_batch_launch_c2(b, sms, smem, s);
+    default: return lane_batch_launch_c3(b, sms, smem, s);
+    }
+}
+
 // Work items for configuration k: every (beam, linear tile) of the beams that
 // can use it, heaviest beams (most channels per item) first.
 static int batch_build(dd_batch *B, int k)
@@ -609,7 +636,7 @@ static int batch_build(dd_batch *B, int k)
     B->sep.clear();
     for (int i = 0; i < (int)B->plans.size(); ++i) {
         const FastPlan *f = fp(B->plans[i]);
-        if (k >= 0 && f && f->cfg[k].ok) B->k2.push_back(i); else B->sep.push_back(i);
+        if (batch_geom(f, k).ok) B->k2.push_back(i); else B->sep.push_back(i);
     }
     std::vector<int> order = B->k2;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
@@ -619,8 +646,8 @@ static int batch_build(dd_batch *B, int k)
     int bar_off = 0;
     for (int i : order) {
         const dd_plan *p = B->plans[i];
-        const FastCfgData &c = fp(p)->cfg[k];
-        const int64_t ntile = (p->nsamp_out + 32 * c.tr - 1) / (32 * c.tr);
+        const BatchGeom c = batch_geom(fp(p), k);
+        const int64_t ntile = (p->nsamp_out + c.tile - 1) / c.tile;
         const int64_t n = ntile * c.nblk;
         if ((int64_t)items.size() + n > INT32_MAX) return set_error(DD_ERR_ARG, "batch too large");
         for (int64_t l = 0; l < n; ++l) items.push_back(make_uint2((unsigned)i, (unsigned)l));
@@ -646,8 +673,8 @@ static int batch_prepare(dd_batch *B)
 {
     for (int i : B->k2) {
         dd_plan *p = B->plans[i];
-        const FastCfgData &c = fp(p)->cfg[B->cfg];
-        const int64_t ntile = (p->nsamp_out + 32 * c.tr - 1) / (32 * c.tr);
+        const BatchGeom c = batch_geom(fp(p), B->cfg);
+        const int64_t ntile = (p->nsamp_out + c.tile - 1) / c.tile;
         int rc = ensure_partials_public(p, ntile * c.nblk);
         if (rc) return rc;
     }
@@ -664,7 +691,40 @@ static int batch_enqueue(dd_batch *B, const void *const *ins, const int64_t *pit
     int rc = batch_prepare(B);
     if (rc) return rc;
     std::vector<int> own(B->sep);
-    if (B->cfg >= 0) {
+    if (B->cfg >= kNumFastCfg) {
+        const int kl = B->cfg - kNumFastCfg;
+        for (int i : B->k2) {
+            dd_plan *p = B->plans[i];
+            FastPlan *f = fp(p);
+            if (((uintptr_t)ins[i] & 15u) || (pitches[i] % f->al))
+                return set_error(DD_ERR_ARG, "beam %d: input rows must be 16-byte aligned in a batch", i);
+            const LaneCfgData &c = f->lane[kl];
+            LaneLaunch &a = B->h_lbeams[i];
+            a.in = ins[i]; a.pitch = pitches[i];
+            a.nsamp_in_al = (p->nsamp_in + f->al - 1) / f->al * f->al;
+            a.nchans = p->nchans; a.ndm = p->ndm; a.nout = p->nsamp_out;
+            a.offs = c.d_offs; a.base = c.d_base;
+            a.rs = c.rs; a.ch = c.ch; a.bar_off = B->bar_off; a.nblk = c.nblk;
+            a.ntile = (p->nsamp_out + 32 * c.ti - 1) / (32 * c.ti);
+            a.dgroup = std::max(1, std::min(f->dgroup, c.nblk));
+            a.out = outs[i]; a.partials = p->d_partials; a.err = f->d_err; a.smem = B->smem;
+            a.dtype = (int)p->dtype;
+        }
+        cudaError_t e = cudaMemcpyAsync(B->d_lbeams, B->h_lbeams, B->plans.size() * sizeof(LaneLaunch),
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned int), s);
+        if (e != cudaSuccess) return cuda_fail(e, "batch setup");
+        LaneBatchLaunch bl;
+        bl.beams = B->d_lbeams; bl.items = B->d_items; bl.nitems = B->nitems;
+        bl.bar_off = B->bar_off; bl.counter = B->d_counter;
+        e = batch_launch_lane(kl, bl, B->grid, B->smem, s);
+        if (e != cudaSuccess) return cuda_fail(e, "launch lane_batch_kernel");
+        for (int i : B->k2) {
+            dd_plan *p = B->plans[i];
+            p->n_partials = B->h_lbeams[i].ntile * B->h_lbeams[i].nblk;
+            p->stats_out = outs[i];
+        }
+    } else if (B->cfg >= 0) {
         for (int i : B->k2) {
             dd_plan *p = B->plans[i];
             FastPlan *f = fp(p);
@@ -733,27 +793,33 @@ int dd_batch_create(dd_plan *const *plans, int32_t nplans, dd_batch **out)
     B->plans.assign(plans, plans + nplans);
     B->device = dev;
     B->grid = std::max(1, plans[0]->sm_count);
-    // first configuration every kernel-2 beam can use
+    // first configuration, in the order of measured speed (kernel 3 shapes,
+    // then kernel 2), that every tiled-kernel beam can use
+    static const int pref[] = {kNumFastCfg + 2, kNumFastCfg + 0, kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
     int k = -1;
-    for (int c = 0; c < kNumFastCfg && k < 0; ++c) {
+    for (int c : pref) {
+        if (k >= 0) break;
         bool all = false, some = false;
         for (int i = 0; i < nplans; ++i) {
             const FastPlan *f = fp(plans[i]);
             if (!f) continue;
             some = true;
-            all = f->cfg[c].ok;
+            all = batch_geom(f, c).ok;
             if (!all) break;
         }
         if (some && all) k = c;
     }
     cudaError_t e = cudaMalloc(&B->d_beams, nplans * sizeof(FastLaunch));
     if (e == cudaSuccess) e = cudaMallocHost(&B->h_beams, nplans * sizeof(FastLaunch));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_lbeams, nplans * sizeof(LaneLaunch));
+    if (e == cudaSuccess) e = cudaMallocHost(&B->h_lbeams, nplans * sizeof(LaneLaunch));
     if (e == cudaSuccess) e = cudaMalloc(&B->d_counter, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&B->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(B->d_err, 0, sizeof(int));
     int rc = e == cudaSuccess ? DD_OK : cuda_fail(e, "batch allocation");
     if (rc == DD_OK) {
         memset(B->h_beams, 0, nplans * sizeof(FastLaunch));
+        memset(B->h_lbeams, 0, nplans * sizeof(LaneLaunch));
         rc = batch_build(B, k);
     }
     if (rc != DD_OK) { dd_batch_destroy(B); return rc; }
@@ -770,6 +836,8 @@ int dd_batch_destroy(dd_batch *B)
     if (B->d_items) cudaFree(B->d_items);
     if (B->d_beams) cudaFree(B->d_beams);
     if (B->h_beams) cudaFreeHost(B->h_beams);
+    if (B->d_lbeams) cudaFree(B->d_lbeams);
+    if (B->h_lbeams) cudaFreeHost(B->h_lbeams);
     if (B->d_counter) cudaFree(B->d_counter);
     if (B->d_err) cudaFree(B->d_err);
     delete B;
@@ -837,11 +905,11 @@ int dd_batch_autotune(dd_batch *B, const void *const *ins, const int64_t *pitche
         return set_error(DD_ERR_CUDA, "cudaEventCreate");
     float best = 1e30f;
     int bk = B->cfg, rc = DD_OK;
-    for (int k = 0; k < kNumFastCfg && rc == DD_OK; ++k) {
+    for (int k = 0; k < kLaneEnd && rc == DD_OK; ++k) {
         bool all = true;
         for (int i = 0; i < (int)B->plans.size(); ++i) {
             const FastPlan *f = fp(B->plans[i]);
-            if (f && !f->cfg[k].ok) all = false;
+            if (f && !batch_geom(f, k).ok) all = false;
         }
         if (!all) continue;
         rc = batch_build(B, k);
@@ -858,6 +926,16 @@ int dd_batch_autotune(dd_batch *B, const void *const *ins, const int64_t *pitche
     if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
     if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
     return batch_build(B, bk);
+}
+
+int dd_batch_set_config(dd_batch *B, int32_t config)
+{
+    if (!B) return set_error(DD_ERR_ARG, "batch is NULL");
+    if (config < 0 || config >= kLaneEnd) return set_error(DD_ERR_ARG, "batch configuration %d out of range", config);
+    cudaDeviceSynchronize();
+    if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+    if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+    return batch_build(B, config);
 }
 
 int dd_batch_info(const dd_batch *B, int32_t *config, int64_t *nitems, int32_t *n_separate)

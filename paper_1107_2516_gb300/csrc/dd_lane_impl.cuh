@@ -29,6 +29,7 @@ struct LaneLaunch {
     void *out, *partials;
     int *err;
     size_t smem;
+    int dtype;             // dd_dtype of `in` (batched launches)
 };
 
 template <typename Tin> __device__ __forceinline__ float lane_ld(const Tin *p);
@@ -36,39 +37,42 @@ template <> __device__ __forceinline__ float lane_ld<float>(const float *p) { re
 template <> __device__ __forceinline__ float lane_ld<__half>(const __half *p) { return __half2float(*p); }
 template <> __device__ __forceinline__ float lane_ld<uint8_t>(const uint8_t *p) { return (float)*p; }
 
-template <typename Tin, bool kInt, int TI, int DR, int NW, int MINB>
-__global__ void __launch_bounds__(NW * 32, MINB) lane_kernel(LaneLaunch a)
+// DM block / time tile of linear block index `lin` (DM blocks in groups, time
+// tiles slowest within a group, as kernel 2).
+template <int TI>
+__device__ __forceinline__ void lane_raster(const LaneLaunch &a, int64_t lin, int &blk, int64_t &t0)
 {
-    constexpr int kTile = 32 * TI, kDmBlk = DR * NW;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const Tin *__restrict__ in = static_cast<const Tin *>(a.in);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nchans = a.nchans, rs = a.rs, ch = a.ch;
-
-    // raster (as kernel 2): DM blocks in groups, time tiles slowest within a group
-    const int64_t lin = blockIdx.x;
     const int64_t per_group = (int64_t)a.dgroup * a.ntile;
     const int64_t grp = lin / per_group;
     const int64_t rr = lin - grp * per_group;
     const int gsize = min(a.dgroup, a.nblk - (int)grp * a.dgroup);
-    const int blk = (int)grp * a.dgroup + (int)(rr % gsize);
-    const int64_t t0 = (rr / gsize) * kTile;
+    blk = (int)grp * a.dgroup + (int)(rr % gsize);
+    t0 = (rr / gsize) * (32 * TI);
+}
+
+// One work item: DM block `blk` x the time tile at t0 of the plan in `a`;
+// partials record `lin`.  `gstage` is the block's running stage count (the
+// mbarrier ring persists across the items of a persistent block: stage s
+// of this item uses buffer (gstage+s) % kStages, parity (gstage+s) / kStages).
+// Returns false if a bounded wait gave up.
+template <typename Tin, bool kInt, int TI, int DR, int NW>
+__device__ __forceinline__ bool lane_tile(const LaneLaunch &a, int blk, int64_t t0, int64_t lin,
+                                          unsigned char *smem, uint64_t *bar, uint32_t &gstage)
+{
+    constexpr int kDmBlk = DR * NW;
+    const Tin *__restrict__ in = static_cast<const Tin *>(a.in);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nchans = a.nchans, rs = a.rs, ch = a.ch;
     const int dm0 = blk * kDmBlk;
 
     // layout: [kStages][ch][rs] Tin rows | [kStages][ch][kDmBlk] int32 offsets | mbar at bar_off
     const size_t stage_elems = (size_t)ch * rs;
     Tin *rows = reinterpret_cast<Tin *>(smem);
     int32_t *soffs = reinterpret_cast<int32_t *>(smem + kStages * stage_elems * sizeof(Tin));
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.bar_off);
     const int32_t *boffs = a.offs + (size_t)blk * nchans * kDmBlk;
     const int32_t *bbase = a.base + (size_t)blk * nchans;
     const int nst = (nchans + ch - 1) / ch;
-
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
+    const uint32_t g0 = gstage;
 
     auto row_bytes = [&](int c, int64_t &g) -> uint32_t {
         g = t0 + bbase[c];
@@ -77,7 +81,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) lane_kernel(LaneLaunch a)
         return (uint32_t)(n * (int64_t)sizeof(Tin));
     };
     auto issue = [&](int s) {
-        const int buf = s % kStages;
+        const int buf = (int)((g0 + s) % kStages);
         const int c0 = s * ch;
         const int cn = min(ch, nchans - c0);
         uint32_t bytes = (uint32_t)(cn * kDmBlk * sizeof(int32_t));
@@ -106,8 +110,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) lane_kernel(LaneLaunch a)
     bool ok = true;
     for (int s = 0; s < nst; ++s) {
         if (tid == 0 && s + kStages - 1 < nst) issue(s + kStages - 1);
-        const int buf = s % kStages;
-        if (!mbar_wait(&bar[buf], (uint32_t)((s / kStages) & 1), a.err)) { ok = false; break; }
+        const uint32_t g = g0 + s;
+        const int buf = (int)(g % kStages);
+        if (!mbar_wait(&bar[buf], (g / kStages) & 1u, a.err)) { ok = false; break; }
         const int cn = min(ch, nchans - s * ch);
         const Tin *srow = rows + (size_t)buf * stage_elems + lane;
         const int32_t *so = soffs + (size_t)buf * ch * kDmBlk + warp * DR;
@@ -131,7 +136,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) lane_kernel(LaneLaunch a)
         }
         __syncthreads();
     }
-    if (!ok) return;
+    gstage = g0 + nst;
+    if (!ok) return false;
 
     // epilogue: lanes hold consecutive samples, so stores are coalesced directly
     const int64_t nout = a.nout;
@@ -182,6 +188,80 @@ __global__ void __launch_bounds__(NW * 32, MINB) lane_kernel(LaneLaunch a)
         }
         block_stat_f32(n, s, q, reinterpret_cast<StatF *>(a.partials) + lin);
     }
+    return true;
+}
+
+// One plan: one block per work item, grid = nblk * ntile.
+template <typename Tin, bool kInt, int TI, int DR, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) lane_kernel(LaneLaunch a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.bar_off);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int blk;
+    int64_t t0;
+    lane_raster<TI>(a, blockIdx.x, blk, t0);
+    uint32_t gstage = 0;
+    lane_tile<Tin, kInt, TI, DR, NW>(a, blk, t0, blockIdx.x, smem, bar, gstage);
+}
+
+// lane_tile as an out-of-line function: the persistent kernel calls one per
+// input type, each compiled with the full register budget.
+template <typename Tin, bool kInt, int TI, int DR, int NW>
+__device__ __noinline__ bool lane_tile_call(const LaneLaunch &a, int blk, int64_t t0, int64_t lin,
+                                            unsigned char *smem, uint64_t *bar, uint32_t &gstage)
+{
+    return lane_tile<Tin, kInt, TI, DR, NW>(a, blk, t0, lin, smem, bar, gstage);
+}
+
+// Batched plans with kernel 3: a persistent grid (MINB blocks per SM) pulls
+// work items (beam, linear tile index) from a device queue, heaviest beams
+// first; each beam brings its own tables, buffers and input type.
+struct LaneBatchLaunch {
+    const LaneLaunch *beams;
+    const uint2 *items;
+    int nitems;
+    int bar_off;
+    unsigned int *counter;
+};
+
+template <int TI, int DR, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) lane_batch_kernel(LaneBatchLaunch b)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_item;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + b.bar_off);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t gstage = 0;
+    while (true) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(b.counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= b.nitems) break;
+        const uint2 w = b.items[it];
+        const LaneLaunch &a = b.beams[w.x];
+        int blk;
+        int64_t t0;
+        lane_raster<TI>(a, w.y, blk, t0);
+        bool ok;
+        switch (a.dtype) {
+        case DD_F32: ok = lane_tile_call<float, false, TI, DR, NW>(a, blk, t0, w.y, smem, bar, gstage); break;
+        case DD_F16: ok = lane_tile_call<__half, false, TI, DR, NW>(a, blk, t0, w.y, smem, bar, gstage); break;
+        default: ok = lane_tile_call<uint8_t, true, TI, DR, NW>(a, blk, t0, w.y, smem, bar, gstage); break;
+        }
+        if (!ok) break;
+        __syncthreads();
+        if (threadIdx.x == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
 }
 
 template <int TI, int DR, int NW, int MINB>
@@ -204,7 +284,18 @@ cudaError_t lane_prepare_cfg(size_t optin)
         e = allow_max_dynamic_smem((const void *)lane_kernel<__half, false, TI, DR, NW, MINB>, optin);
     if (e == cudaSuccess)
         e = allow_max_dynamic_smem((const void *)lane_kernel<uint8_t, true, TI, DR, NW, MINB>, optin);
+    if (e == cudaSuccess)
+        e = allow_max_dynamic_smem((const void *)lane_batch_kernel<TI, DR, NW, MINB>, optin);
     return e;
+}
+
+// Persistent launch: grid = MINB blocks per SM (the occupancy the shared
+// memory budget of the configuration allows).
+template <int TI, int DR, int NW, int MINB>
+cudaError_t lane_batch_launch_cfg(const LaneBatchLaunch &b, int sms, size_t smem, cudaStream_t s)
+{
+    lane_batch_kernel<TI, DR, NW, MINB><<<sms * MINB, NW * 32, smem, s>>>(b);
+    return cudaGetLastError();
 }
 
 // Configurations compiled into the library: {samples per lane, DM trials per
@@ -221,5 +312,9 @@ cudaError_t lane_prepare_c0(size_t optin);
 cudaError_t lane_prepare_c1(size_t optin);
 cudaError_t lane_prepare_c2(size_t optin);
 cudaError_t lane_prepare_c3(size_t optin);
+cudaError_t lane_batch_launch_c0(const LaneBatchLaunch &b, int sms, size_t smem, cudaStream_t s);
+cudaError_t lane_batch_launch_c1(const LaneBatchLaunch &b, int sms, size_t smem, cudaStream_t s);
+cudaError_t lane_batch_launch_c2(const LaneBatchLaunch &b, int sms, size_t smem, cudaStream_t s);
+cudaError_t lane_batch_launch_c3(const LaneBatchLaunch &b, int sms, size_t smem, cudaStream_t s);
 
 }  // namespace dd

@@ -59,11 +59,15 @@ def _bufs(data, plans):
     return ins, [pitch for _, _, pitch in data], outs
 
 
-def test_batch_matches_single_plans_and_graph(beams):
+@pytest.mark.parametrize("config", [None, 1, 5, 3])
+def test_batch_matches_single_plans_and_graph(beams, config):
+    # default configuration, a kernel 2 shape, kernel 3 shapes
     plans = _plans(beams)
     batch = dd.Batch(plans)
+    if config is not None:
+        batch.set_config(config)
     cfg, nitems, nsep = batch.info
-    assert cfg >= 0 and nitems > 0 and nsep == 0
+    assert cfg == (5 if config is None else config) and nitems > 0 and nsep == 0
     for p in plans:
         p.set_tile(cfg, 8)
     ins, pitches, outs = _bufs(beams, plans)
