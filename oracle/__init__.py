@@ -14,6 +14,7 @@ Paper passages followed (Magro et al. 2011):
   Section 3 (output thread) mean, sigma, n-sigma test -> stats(), search()
   Section 3.2              subband de-dispersion     -> subband_tables(), subband_dedisperse()
   Section 3.2, Table 1     binning, survey passes    -> bin_samples(), survey_passes()
+  Section 5, Tables 5-6    channelise, power, corner turn -> channelise_power()
 """
 from __future__ import annotations
 
@@ -300,3 +301,24 @@ def survey_passes(passes) -> list:
         n = int(round((hi - lo) / step))
         out.append(([lo + i * step for i in range(n)], int(nb), int(round(sub / step))))
     return out
+
+
+def channelise_power(volts: np.ndarray, nfft: int) -> np.ndarray:
+    """Front end of the real-time pipeline (Section 5, Tables 5-6):
+    channelisation, intensity, corner turn.
+
+    volts: complex [npol][nsub][n] baseband voltages (upper sideband).  Each
+    subband's stream is cut into blocks of nfft samples and transformed (the
+    FFT is the channeliser); the intensity is |X|^2 summed over polarisations;
+    the result is written channel-major ("corner turn") as
+    out[s*nfft + j][b], j ordering the subband's nfft channels by DEScending
+    frequency: FFT bin k has offset k (k < nfft/2) or k - nfft (k >= nfft/2),
+    so channel j holds bin (nfft/2 - 1 - j) mod nfft.  Float64."""
+    v = np.asarray(volts)
+    npol, nsub, n = v.shape
+    nb = n // nfft
+    x = v[:, :, :nb * nfft].astype(np.complex128).reshape(npol, nsub, nb, nfft)
+    p = (np.abs(np.fft.fft(x, axis=-1)) ** 2).sum(axis=0)          # [nsub][nb][nfft]
+    order = [(nfft // 2 - 1 - j) % nfft for j in range(nfft)]
+    p = p[:, :, order]                                               # descending frequency
+    return np.ascontiguousarray(p.transpose(0, 2, 1).reshape(nsub * nfft, nb))
