@@ -444,6 +444,26 @@ DD_API int dd_survey_search(dd_survey_plan *plan, int32_t pass, const void *out_
 /* mu and sigma used by the last dd_survey_search of pass `pass`. */
 DD_API int dd_survey_last_stats(const dd_survey_plan *plan, int32_t pass, double *mu, double *sigma);
 
+/* ---------------------------------------------------------------------
+ * Front end of the real-time pipeline (Section 5, Tables 5-6): channeliser,
+ * intensity and corner turn in one pass.
+ *
+ * volt_dev: complex64 baseband voltages [npol][nsub][nsamp] (interleaved
+ * float32 re, im; device, 16-byte aligned; nsamp even), each subband sampled
+ * in upper sideband.  Each subband's stream is cut into blocks of nfft
+ * samples (nfft in {2, 4, 8, 16, 32}; trailing samples dropped) and
+ * transformed by an nfft-point forward FFT (the paper's channeliser); the
+ * intensity |X|^2 is summed over the npol (1 or 2) polarisations; the result
+ * is written channel-major ("corner turn") to out_dev [nsub*nfft][out_pitch]
+ * float32 (device, caller-owned, out_pitch >= nsamp/nfft): row s*nfft + j
+ * holds the subband's j-th channel in DEScending frequency (FFT bin
+ * (nfft/2 - 1 - j) mod nfft), column b the b-th block.  With subbands ordered
+ * from the top of the band down, the rows form a standard descending-band
+ * filterbank ready for dd_execute (sampling time nfft x the subband's).
+ * Asynchronous on `stream`.  DD_ERR_ARG for invalid arguments. */
+DD_API int dd_channelise(const void *volt_dev, int32_t npol, int32_t nsub, int64_t nsamp, int32_t nfft,
+                         float *out_dev, int64_t out_pitch, void *stream);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 DD_API const char *dd_last_error(void);
 

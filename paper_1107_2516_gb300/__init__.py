@@ -8,7 +8,7 @@ from .dd import (Batch, CANDIDATE_DTYPE, CHUNK_RESULT_DTYPE, DD_PRIMING, Server,
                  DD_F32, DD_U8, DDError, EXPORTS, Plan, dd_execute, dd_last_error, dd_last_stats,
                  dd_plan_autotune, dd_plan_create, dd_plan_destroy, dd_plan_get_kernel,
                  dd_plan_get_tile, dd_plan_info, dd_plan_set_kernel, dd_plan_set_tile, dd_process_host,
-                 dd_search, dd_stats_f32_noalloc, dd_subband_execute, dd_subband_last_stats,
+                 dd_channelise, dd_search, dd_stats_f32_noalloc, dd_subband_execute, dd_subband_last_stats,
                  dd_subband_plan_create, dd_subband_plan_destroy, dd_subband_plan_info,
                  dd_subband_search, dd_version, load)
 
@@ -16,7 +16,7 @@ __all__ = ["Batch", "CANDIDATE_DTYPE", "CHUNK_RESULT_DTYPE", "DD_PRIMING", "Serv
            "DD_F16", "DD_F32", "DD_U8", "DDError", "EXPORTS", "Plan",
            "dd_execute", "dd_last_error", "dd_last_stats", "dd_plan_autotune", "dd_plan_create",
            "dd_plan_destroy", "dd_plan_get_kernel", "dd_plan_get_tile", "dd_plan_info",
-           "dd_plan_set_kernel", "dd_plan_set_tile", "dd_process_host", "dd_search",
+           "dd_plan_set_kernel", "dd_plan_set_tile", "dd_process_host", "dd_search", "dd_channelise",
            "dd_stats_f32_noalloc", "dd_subband_execute", "dd_subband_last_stats",
            "dd_subband_plan_create", "dd_subband_plan_destroy", "dd_subband_plan_info",
            "dd_subband_search", "dd_version", "load"]

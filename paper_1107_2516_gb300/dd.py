@@ -36,7 +36,7 @@ EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "d
            "dd_server_memory", "dd_subband_plan_create", "dd_subband_plan_destroy",
            "dd_subband_plan_info", "dd_subband_execute", "dd_subband_search", "dd_subband_last_stats",
            "dd_survey_plan_create", "dd_survey_plan_destroy", "dd_survey_pass_info", "dd_survey_execute",
-           "dd_survey_search", "dd_survey_last_stats")
+           "dd_survey_search", "dd_survey_last_stats", "dd_channelise")
 
 DD_PRIMING = 7
 
@@ -120,6 +120,7 @@ def load(path: Optional[str] = None):
             "dd_survey_execute": (C.c_int, [vp, vp, i64, vp, vp]),
             "dd_survey_search": (C.c_int, [vp, i32, vp, vp, i64, P64, vp]),
             "dd_survey_last_stats": (C.c_int, [vp, i32, C.POINTER(f64), C.POINTER(f64)]),
+            "dd_channelise": (C.c_int, [vp, i32, i32, i64, i32, vp, i64, vp]),
             "dd_last_error": (C.c_char_p, []),
             "dd_version": (C.c_char_p, []),
         }
@@ -677,3 +678,13 @@ class SurveyPlan:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ front end (Section 5)
+
+def dd_channelise(volt_dev, npol: int, nsub: int, nsamp: int, nfft: int, out_dev, out_pitch: int,
+                  stream=None) -> None:
+    """Channeliser + intensity + corner turn: complex64 [npol][nsub][nsamp] ->
+    float32 [nsub*nfft][out_pitch] (descending frequency within each subband)."""
+    _check(load().dd_channelise(_ptr(volt_dev), int(npol), int(nsub), int(nsamp), int(nfft), _ptr(out_dev),
+                                int(out_pitch), _stream(stream)))
