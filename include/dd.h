@@ -143,8 +143,24 @@ DD_API int dd_execute(dd_plan *plan, const void *in_dev, int64_t in_pitch, void 
 DD_API int dd_search(dd_plan *plan, const void *out_dev, dd_candidate *cand_host,
               int64_t capacity, int64_t *n_found, void *stream);
 
-/* mu and sigma used by the last dd_search on this plan (Section 3). */
+/* mu and sigma used by the last dd_search on this plan (Section 3; the
+ * whole buffer's statistics also when per-row statistics are enabled). */
 DD_API int dd_last_stats(const dd_plan *plan, double *mu, double *sigma);
+
+/* Search variant: per_row = 1 makes dd_search (and the batch / server
+ * searches of this plan) use each DM row's own mean and population standard
+ * deviation instead of the whole buffer's (Section 3 uses the whole buffer):
+ * T_w(row) = w*mu_row + k*sigma_row*sqrt(w), S/N = (B_w - w*mu_row) /
+ * (sigma_row*sqrt(w)).  Robust to DM-dependent baselines (low-DM rows carry
+ * more interference in real data).  One extra read of `out` per search.
+ * per_row = 0 restores the whole-buffer statistics.  Allocates
+ * ndm x 784 bytes of device and pinned host scratch on first enabling. */
+DD_API int dd_plan_set_search_stats(dd_plan *plan, int32_t per_row);
+
+/* Per-row mean and standard deviation used by the last dd_search (host
+ * arrays of ndm doubles, either may be NULL); DD_ERR_ARG unless per-row
+ * statistics are enabled. */
+DD_API int dd_last_row_stats(const dd_plan *plan, double *mu_rows, double *sigma_rows);
 
 /* End-to-end call with HOST buffers: copies in_host (pinned or pageable,
  * channel-major, in_pitch elements per row) to the device, runs dd_execute
@@ -331,6 +347,31 @@ DD_API int dd_server_memory(dd_server *server, int64_t *used, int64_t *budget);
  * the GPU (different streams, no ordering between them) race and may return
  * wrong values; calls ordered on one stream are safe. */
 DD_API int dd_stats_f32_noalloc(const float *x_dev, int64_t n, double *mu_sigma_dev, void *stream);
+
+/* ---------------------------------------------------------------------
+ * Candidate clustering (search variant, host side).  Section 3's test
+ * reports every point above the threshold, so one pulse gives many
+ * neighbouring (DM, time, width) points.  Friends-of-friends: candidates
+ * whose DM indices differ by at most dm_link and times by at most t_link
+ * (samples; any widths) are linked; clusters are the connected components.
+ * Each cluster: its strongest member (largest S/N; ties: smallest
+ * (dm_idx, t, width_idx)), member count and DM / time extent.  Clusters are
+ * written sorted by their strongest member's (dm_idx, t, width_idx); labels
+ * (optional, [n]) receives each candidate's cluster index in that order.
+ * Host arrays, caller-owned; no device work.  DD_ERR_OVERFLOW (and the true
+ * count in *n_clusters) if more than `capacity` clusters. */
+typedef struct {
+    int32_t dm_idx, width_idx;   /* strongest member */
+    int64_t t;
+    float snr;
+    int32_t n_members;
+    int32_t dm_lo, dm_hi;        /* extent, inclusive */
+    int64_t t_lo, t_hi;
+} dd_cluster;
+
+DD_API int dd_cluster_candidates(const dd_candidate *cands, int64_t n, int32_t dm_link, int64_t t_link,
+                                 dd_cluster *clusters, int64_t capacity, int64_t *n_clusters,
+                                 int64_t *labels);
 
 /* ---------------------------------------------------------------------
  * Subband de-dispersion (Section 3.2): the paper's two-stage approximation

@@ -322,3 +322,56 @@ def channelise_power(volts: np.ndarray, nfft: int) -> np.ndarray:
     order = [(nfft // 2 - 1 - j) % nfft for j in range(nfft)]
     p = p[:, :, order]                                               # descending frequency
     return np.ascontiguousarray(p.transpose(0, 2, 1).reshape(nsub * nfft, nb))
+
+
+def search_per_row(out: np.ndarray, widths, k: float, cap: int = 1 << 20):
+    """Search variant with per-DM-row statistics: each row's population mean
+    and standard deviation (stats() of the row) set its thresholds
+    T_w = w*mu_row + k*sigma_row*sqrt(w); otherwise search().  Returns
+    (candidates sorted by (dm, t, width_idx), mu [ndm], sigma [ndm])."""
+    x = np.ascontiguousarray(out)
+    ndm = x.shape[0]
+    mus, sgs, parts = np.empty(ndm), np.empty(ndm), []
+    for j in range(ndm):
+        mus[j], sgs[j] = stats(x[j:j + 1])
+        c = search(x[j:j + 1], widths, mus[j], sgs[j], k, cap)
+        c["dm_idx"] = j
+        parts.append(c)
+    cands = np.concatenate(parts) if parts else np.empty(0, CAND_DTYPE)
+    return cands, mus, sgs
+
+
+def cluster(cands: np.ndarray, dm_link: int, t_link: int):
+    """Friends-of-friends clustering of candidates (search variant): pairs with
+    |d dm_idx| <= dm_link and |d t| <= t_link are linked; clusters are the
+    connected components.  Every pair is tested (plain O(n^2)).  Returns a list
+    of (strongest member index, member indices, dm range, t range) sorted by the
+    strongest member's (dm_idx, t, width_idx); the strongest member has the
+    largest snr, ties to the smallest (dm_idx, t, width_idx)."""
+    n = len(cands)
+    parent = list(range(n))
+
+    def find(a):
+        while parent[a] != a:
+            a = parent[a]
+        return a
+
+    for i in range(n):
+        for j in range(i + 1, n):
+            if (abs(int(cands[i]["dm_idx"]) - int(cands[j]["dm_idx"])) <= dm_link and
+                    abs(int(cands[i]["t"]) - int(cands[j]["t"])) <= t_link):
+                a, b = find(i), find(j)
+                if a != b:
+                    parent[max(a, b)] = min(a, b)
+    groups = {}
+    for i in range(n):
+        groups.setdefault(find(i), []).append(i)
+    key = lambda i: (int(cands[i]["dm_idx"]), int(cands[i]["t"]), int(cands[i]["width_idx"]))
+    out = []
+    for members in groups.values():
+        best = min(members, key=lambda i: (-float(cands[i]["snr"]),) + key(i))
+        dms = [int(cands[i]["dm_idx"]) for i in members]
+        ts = [int(cands[i]["t"]) for i in members]
+        out.append((best, sorted(members), (min(dms), max(dms)), (min(ts), max(ts))))
+    out.sort(key=lambda g: key(g[0]))
+    return out

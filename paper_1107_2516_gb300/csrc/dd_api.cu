@@ -75,6 +75,8 @@ static void free_plan(dd_plan *p)
     if (p->d_count) cudaFree(p->d_count);
     if (p->h_count) cudaFreeHost(p->h_count);
     if (p->h_params) cudaFreeHost(p->h_params);
+    if (p->d_rowprm) cudaFree(p->d_rowprm);
+    if (p->h_rowprm) cudaFreeHost(p->h_rowprm);
     if (p->d_in_stage) cudaFree(p->d_in_stage);
     if (p->d_out_stage) cudaFree(p->d_out_stage);
     delete p;
@@ -101,6 +103,9 @@ int search_readback(dd_plan *plan, dd_candidate *cand_host, int64_t capacity, in
                                     cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(plan->h_params, plan->d_params, sizeof(SearchParams), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && plan->row_stats && plan->d_rowprm)
+        e = cudaMemcpyAsync(plan->h_rowprm, plan->d_rowprm, (size_t)plan->ndm * sizeof(RowParams),
+                            cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "search readback");
     int rc = fast_error(plan, s);
@@ -371,6 +376,36 @@ int dd_search(dd_plan *plan, const void *out_dev, dd_candidate *cand_host, int64
     plan->cand_cap = saved_cap;
     if (rc) return rc;
     return search_readback(plan, cand_host, capacity, n_found, s, dev_cap);
+}
+
+int dd_plan_set_search_stats(dd_plan *plan, int32_t per_row)
+{
+    if (!plan) return set_error(DD_ERR_ARG, "plan is NULL");
+    if (per_row != 0 && per_row != 1) return set_error(DD_ERR_ARG, "per_row must be 0 or 1");
+    if (per_row && !plan->d_rowprm) {
+        cudaError_t e = cudaMalloc(&plan->d_rowprm, (size_t)plan->ndm * sizeof(RowParams));
+        if (e == cudaSuccess) e = cudaMallocHost(&plan->h_rowprm, (size_t)plan->ndm * sizeof(RowParams));
+        if (e == cudaSuccess) memset(plan->h_rowprm, 0, (size_t)plan->ndm * sizeof(RowParams));
+        if (e != cudaSuccess) {
+            if (plan->d_rowprm) cudaFree(plan->d_rowprm);
+            plan->d_rowprm = nullptr;
+            plan->h_rowprm = nullptr;
+            return cuda_fail(e, "per-row statistics scratch");
+        }
+    }
+    plan->row_stats = per_row;
+    return DD_OK;
+}
+
+int dd_last_row_stats(const dd_plan *plan, double *mu_rows, double *sigma_rows)
+{
+    if (!plan) return set_error(DD_ERR_ARG, "plan is NULL");
+    if (!plan->row_stats || !plan->h_rowprm) return set_error(DD_ERR_ARG, "per-row statistics are not enabled");
+    for (int i = 0; i < plan->ndm; ++i) {
+        if (mu_rows) mu_rows[i] = plan->h_rowprm[i].mu;
+        if (sigma_rows) sigma_rows[i] = plan->h_rowprm[i].sigma;
+    }
+    return DD_OK;
 }
 
 int dd_last_stats(const dd_plan *plan, double *mu, double *sigma)

@@ -29,6 +29,14 @@ struct SearchParams {
 
 constexpr int kMaxWidths = 64;
 
+// Per-DM-row statistics and thresholds (search option: statistics of each DM
+// row instead of the whole buffer), same exact float / integer forms.
+struct RowParams {
+    double mu, sigma;
+    float thr_f[kMaxWidths];
+    long long thr_i[kMaxWidths];
+};
+
 // Tile shape of the generic kernel (kernel 1).
 constexpr int kGenDms = 16;      // DM trials per block
 constexpr int kGenThreads = 256; // threads per block
@@ -76,6 +84,10 @@ struct dd_plan {
     unsigned long long *h_count = nullptr; // pinned
     dd::SearchParams *h_params = nullptr;  // pinned
     double last_mu = 0, last_sigma = 0;
+    // per-DM-row statistics option
+    int32_t row_stats = 0;                 // 0: whole buffer (Section 3), 1: per DM row
+    dd::RowParams *d_rowprm = nullptr;     // [ndm]
+    dd::RowParams *h_rowprm = nullptr;     // pinned [ndm], filled by the last search
     // end-to-end staging (dd_process_host)
     void *d_in_stage = nullptr;
     size_t in_stage_bytes = 0;

@@ -275,6 +275,99 @@ finalize_kernel(const void *__restrict__ partials, int64_t np, const int32_t *__
 }
 
 // ---------------------------------------------------------------------------
+// Per-DM-row statistics (search option): one block per row reads the row once.
+// Float rows: each thread sums x - K and (x - K)^2 in FP32 with K its first
+// value (a shift near the mean keeps the second moment free of cancellation),
+// the block merges (n, mean, M2) in FP64.  Integer rows: exact int64 sums,
+// 128-bit merge.  Then mu_row, sigma_row (population) and the row's
+// thresholds T_w = w*mu_row + k*sigma_row*sqrt(w) in the exact float/integer
+// forms of finalize_kernel.
+// ---------------------------------------------------------------------------
+constexpr int kRowThreads = 512;
+
+template <bool kInt>
+__global__ void __launch_bounds__(kRowThreads)
+row_stats_kernel(const void *__restrict__ out_, int64_t nout, const int32_t *__restrict__ widths, int nw,
+                 double k, RowParams *__restrict__ rp)
+{
+    __shared__ double sa[kRowThreads], sb[kRowThreads], sc[kRowThreads];
+    __shared__ double mu_s, sg_s;
+    const int row = blockIdx.x;
+    const int tid = threadIdx.x;
+    if constexpr (kInt) {
+        const int32_t *x = reinterpret_cast<const int32_t *>(out_) + (size_t)row * nout;
+        long long n = 0, s = 0, q = 0;
+        for (int64_t t = tid; t < nout; t += kRowThreads) {
+            const long long v = x[t];
+            n++; s += v; q += v * v;
+        }
+        __shared__ long long sn[kRowThreads], ss[kRowThreads];
+        __shared__ unsigned long long ql[kRowThreads], qh[kRowThreads];
+        sn[tid] = n; ss[tid] = s; ql[tid] = (unsigned long long)q; qh[tid] = 0;
+        __syncthreads();
+        for (int h = kRowThreads / 2; h > 0; h >>= 1) {
+            if (tid < h) {
+                sn[tid] += sn[tid + h];
+                ss[tid] += ss[tid + h];
+                unsigned __int128 a = ((unsigned __int128)qh[tid] << 64) | ql[tid];
+                const unsigned __int128 b = ((unsigned __int128)qh[tid + h] << 64) | ql[tid + h];
+                a += b;
+                ql[tid] = (unsigned long long)a;
+                qh[tid] = (unsigned long long)(a >> 64);
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const long long N = sn[0], S = ss[0];
+            const unsigned __int128 Q = ((unsigned __int128)qh[0] << 64) | ql[0];
+            const __int128 num = (__int128)((unsigned __int128)N * Q) - (__int128)S * (__int128)S;
+            const double dn = (double)N;
+            mu_s = (double)S / dn;
+            sg_s = sqrt((double)num / (dn * dn));
+        }
+    } else {
+        const float *x = reinterpret_cast<const float *>(out_) + (size_t)row * nout;
+        const float K = tid < nout ? x[tid] : 0.f;
+        float s = 0.f, q = 0.f;
+        int n = 0;
+        for (int64_t t = tid; t < nout; t += kRowThreads) {
+            const float d = x[t] - K;
+            s += d; q += d * d; n++;
+        }
+        // thread (n, mean, M2) in double: mean = K + s/n, M2 = q - s^2/n
+        const double dn = (double)n;
+        const double m = n ? (double)K + (double)s / dn : 0.0;
+        const double m2 = n ? fmax((double)q - (double)s * (double)s / dn, 0.0) : 0.0;
+        sa[tid] = dn; sb[tid] = dn * m;
+        __syncthreads();
+        for (int h = kRowThreads / 2; h > 0; h >>= 1) {
+            if (tid < h) { sa[tid] += sa[tid + h]; sb[tid] += sb[tid + h]; }
+            __syncthreads();
+        }
+        const double N = sa[0], M = N > 0 ? sb[0] / N : 0.0;
+        __syncthreads();
+        const double e = m - M;
+        sc[tid] = m2 + dn * e * e;
+        __syncthreads();
+        for (int h = kRowThreads / 2; h > 0; h >>= 1) {
+            if (tid < h) sc[tid] += sc[tid + h];
+            __syncthreads();
+        }
+        if (tid == 0) { mu_s = M; sg_s = sqrt(sc[0] / N); }
+    }
+    __syncthreads();
+    if (tid == 0) { rp[row].mu = mu_s; rp[row].sigma = sg_s; }
+    if (tid < nw) {
+        const double w = (double)widths[tid];
+        const double T = w * mu_s + k * sg_s * sqrt(w);
+        rp[row].thr_f[tid] = __double2float_rd(T);
+        double f = floor(T);
+        f = fmin(fmax(f, -4.0e18), 4.0e18);
+        rp[row].thr_i[tid] = (long long)f;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Boxcar threshold search.  Block = one DM row x kSearchTile samples; thread
 // owns kSearchPer consecutive samples.  For the widths in ascending order it
 // extends B_w at its first sample from the previous width's sum, then slides
@@ -294,8 +387,8 @@ template <bool kInt>
 __global__ void __launch_bounds__(kSearchThreads)
 search_kernel(const void *__restrict__ out_, int64_t nout,
               const int32_t *__restrict__ wsorted, int nw, int wmax,
-              const SearchParams *__restrict__ prm, dd_candidate *__restrict__ cands,
-              int64_t cap, unsigned long long *__restrict__ count)
+              const SearchParams *__restrict__ prm, const RowParams *__restrict__ rp,
+              dd_candidate *__restrict__ cands, int64_t cap, unsigned long long *__restrict__ count)
 {
     using T = typename std::conditional<kInt, int32_t, float>::type;
     using Acc = typename std::conditional<kInt, long long, float>::type;
@@ -310,8 +403,8 @@ search_kernel(const void *__restrict__ out_, int64_t nout,
     if (threadIdx.x < nw) {
         sw[threadIdx.x] = wsorted[threadIdx.x];
         sidx[threadIdx.x] = wsorted[nw + threadIdx.x];
-        thf[threadIdx.x] = prm->thr_f[sidx[threadIdx.x]];
-        thi[threadIdx.x] = prm->thr_i[sidx[threadIdx.x]];
+        thf[threadIdx.x] = rp ? rp[blockIdx.y].thr_f[sidx[threadIdx.x]] : prm->thr_f[sidx[threadIdx.x]];
+        thi[threadIdx.x] = rp ? rp[blockIdx.y].thr_i[sidx[threadIdx.x]] : prm->thr_i[sidx[threadIdx.x]];
     }
     const T *src = reinterpret_cast<const T *>(out_) + (size_t)row * nout;
     for (int i = threadIdx.x; i < len; i += kSearchThreads) {
@@ -359,8 +452,8 @@ search_kernel(const void *__restrict__ out_, int64_t nout,
 template <bool kInt, int K>
 __global__ void __launch_bounds__(kSearchThreads)
 search_pow2_kernel(const void *__restrict__ out_, int64_t nout, const int32_t *__restrict__ wsorted,
-                   const SearchParams *__restrict__ prm, dd_candidate *__restrict__ cands,
-                   int64_t cap, unsigned long long *__restrict__ count)
+                   const SearchParams *__restrict__ prm, const RowParams *__restrict__ rp,
+                   dd_candidate *__restrict__ cands, int64_t cap, unsigned long long *__restrict__ count)
 {
     using T = typename std::conditional<kInt, int32_t, float>::type;
     constexpr int W = 1 << (K - 1);                 // widest boxcar
@@ -375,8 +468,8 @@ search_pow2_kernel(const void *__restrict__ out_, int64_t nout, const int32_t *_
     if (threadIdx.x < K) {
         const int o = wsorted[K + threadIdx.x];     // original index of sorted width 2^threadIdx.x
         sidx[threadIdx.x] = o;
-        thf[threadIdx.x] = prm->thr_f[o];
-        thi[threadIdx.x] = prm->thr_i[o];
+        thf[threadIdx.x] = rp ? rp[blockIdx.y].thr_f[o] : prm->thr_f[o];
+        thi[threadIdx.x] = rp ? rp[blockIdx.y].thr_i[o] : prm->thr_i[o];
     }
     const T *src = reinterpret_cast<const T *>(out_) + (size_t)row * nout + t0;
     const int64_t avail = nout - t0;                // > 0
@@ -388,7 +481,7 @@ search_pow2_kernel(const void *__restrict__ out_, int64_t nout, const int32_t *_
     }
 #pragma unroll
     for (int q = 0; q < kSearchPer; ++q) x[spad(q * kSearchThreads + threadIdx.x)] = r[q];
-    if (threadIdx.x < W - 1) {
+    if ((int)threadIdx.x < W - 1) {
         const int i = kSearchTile + threadIdx.x;
         x[spad(i)] = i < avail ? src[i] : (T)0;
     }
@@ -449,9 +542,9 @@ template <bool kInt, int K>
 static void launch_search_pow2(dim3 grid, cudaStream_t s, const void *out, const dd_plan *p)
 {
     const size_t smem = (size_t)(spad(kSearchTile + (1 << (K - 1)) - 1) + 1) * 4;
-    search_pow2_kernel<kInt, K><<<grid, kSearchThreads, smem, s>>>(out, p->nsamp_out, p->d_wsorted,
-                                                                    p->d_params, p->d_cands, p->cand_cap,
-                                                                    p->d_count);
+    search_pow2_kernel<kInt, K><<<grid, kSearchThreads, smem, s>>>(out, p->nsamp_out, p->d_wsorted, p->d_params,
+                                                                    p->row_stats ? p->d_rowprm : nullptr,
+                                                                    p->d_cands, p->cand_cap, p->d_count);
 }
 
 // K if the plan's widths are exactly {1, 2, ..., 2^(K-1)} with K <= 7, else 0.
@@ -481,12 +574,15 @@ static void launch_search_pow2_k(int K, dim3 grid, cudaStream_t s, const void *o
 
 // S/N of the compacted hits: (B_w - w*mu) / (sigma*sqrt(w)), in double.
 __global__ void cand_snr_kernel(dd_candidate *__restrict__ cands, const unsigned long long *__restrict__ count,
-                                int64_t cap, const int32_t *__restrict__ widths, const SearchParams *__restrict__ prm)
+                                int64_t cap, const int32_t *__restrict__ widths, const SearchParams *__restrict__ prm,
+                                const RowParams *__restrict__ rp)
 {
     const int64_t n = min((int64_t)*count, cap);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double w = (double)widths[cands[i].width_idx];
-        cands[i].snr = (float)((cands[i].value - w * prm->mu) / (prm->sigma * sqrt(w)));
+        const double mu = rp ? rp[cands[i].dm_idx].mu : prm->mu;
+        const double sg = rp ? rp[cands[i].dm_idx].sigma : prm->sigma;
+        cands[i].snr = (float)((cands[i].value - w * mu) / (sg * sqrt(w)));
     }
 }
 
@@ -649,6 +745,18 @@ int search_launch(dd_plan *p, const void *out, cudaStream_t s)
                                                          p->nwidths, p->sigma_k, p->d_params);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch finalize_kernel");
+    const RowParams *rp = nullptr;
+    if (p->row_stats && p->d_rowprm) {
+        if (isint)
+            row_stats_kernel<true><<<(unsigned)p->ndm, kRowThreads, 0, s>>>(out, p->nsamp_out, w_orig, p->nwidths,
+                                                                           p->sigma_k, p->d_rowprm);
+        else
+            row_stats_kernel<false><<<(unsigned)p->ndm, kRowThreads, 0, s>>>(out, p->nsamp_out, w_orig, p->nwidths,
+                                                                            p->sigma_k, p->d_rowprm);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "launch row_stats_kernel");
+        rp = p->d_rowprm;
+    }
     e = cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "memset count");
     int wmax = 0;
@@ -662,13 +770,15 @@ int search_launch(dd_plan *p, const void *out, cudaStream_t s)
         else launch_search_pow2_k<false>(K, grid, s, out, p);
     } else if (isint)
         search_kernel<true><<<grid, kSearchThreads, smem, s>>>(out, p->nsamp_out, p->d_wsorted, p->nwidths,
-                                                               wmax, p->d_params, p->d_cands, p->cand_cap, p->d_count);
+                                                               wmax, p->d_params, rp, p->d_cands, p->cand_cap,
+                                                               p->d_count);
     else
         search_kernel<false><<<grid, kSearchThreads, smem, s>>>(out, p->nsamp_out, p->d_wsorted, p->nwidths,
-                                                                wmax, p->d_params, p->d_cands, p->cand_cap, p->d_count);
+                                                                wmax, p->d_params, rp, p->d_cands, p->cand_cap,
+                                                                p->d_count);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch search_kernel");
-    cand_snr_kernel<<<64, 256, 0, s>>>(p->d_cands, p->d_count, p->cand_cap, w_orig, p->d_params);
+    cand_snr_kernel<<<64, 256, 0, s>>>(p->d_cands, p->d_count, p->cand_cap, w_orig, p->d_params, rp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "launch cand_snr_kernel");
     return DD_OK;

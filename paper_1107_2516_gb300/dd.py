@@ -36,9 +36,15 @@ EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "d
            "dd_server_memory", "dd_subband_plan_create", "dd_subband_plan_destroy",
            "dd_subband_plan_info", "dd_subband_execute", "dd_subband_search", "dd_subband_last_stats",
            "dd_survey_plan_create", "dd_survey_plan_destroy", "dd_survey_pass_info", "dd_survey_execute",
-           "dd_survey_search", "dd_survey_last_stats", "dd_channelise")
+           "dd_survey_search", "dd_survey_last_stats", "dd_channelise",
+           "dd_plan_set_search_stats", "dd_last_row_stats", "dd_cluster_candidates")
 
 DD_PRIMING = 7
+
+CLUSTER_DTYPE = np.dtype([("dm_idx", np.int32), ("width_idx", np.int32), ("t", np.int64),
+                          ("snr", np.float32), ("n_members", np.int32), ("dm_lo", np.int32),
+                          ("dm_hi", np.int32), ("t_lo", np.int64), ("t_hi", np.int64)])
+assert CLUSTER_DTYPE.itemsize == 48
 
 CHUNK_RESULT_DTYPE = np.dtype([("beam", np.int32), ("status", np.int32), ("seq", np.int64),
                                ("n_candidates", np.int64), ("t_submit", np.float64),
@@ -121,6 +127,9 @@ def load(path: Optional[str] = None):
             "dd_survey_search": (C.c_int, [vp, i32, vp, vp, i64, P64, vp]),
             "dd_survey_last_stats": (C.c_int, [vp, i32, C.POINTER(f64), C.POINTER(f64)]),
             "dd_channelise": (C.c_int, [vp, i32, i32, i64, i32, vp, i64, vp]),
+            "dd_plan_set_search_stats": (C.c_int, [vp, i32]),
+            "dd_cluster_candidates": (C.c_int, [vp, i64, i32, i64, vp, i64, P64, vp]),
+            "dd_last_row_stats": (C.c_int, [vp, vp, vp]),
             "dd_last_error": (C.c_char_p, []),
             "dd_version": (C.c_char_p, []),
         }
@@ -468,6 +477,17 @@ class Plan:
     def set_kernel(self, k):
         dd_plan_set_kernel(self.handle, k)
 
+    def set_search_stats(self, per_row: bool):
+        """Search variant: per-DM-row (True) or whole-buffer (False) statistics."""
+        _check(load().dd_plan_set_search_stats(self.handle, 1 if per_row else 0))
+
+    def row_stats(self):
+        """(mu [ndm], sigma [ndm]) of the last per-row search."""
+        mu = np.empty(self.ndm, np.float64)
+        sg = np.empty(self.ndm, np.float64)
+        _check(load().dd_last_row_stats(self.handle, _ptr(mu), _ptr(sg)))
+        return mu, sg
+
     def autotune(self, in_dev, in_pitch, out_dev, stream=None):
         dd_plan_autotune(self.handle, in_dev, in_pitch, out_dev, stream)
 
@@ -688,3 +708,18 @@ def dd_channelise(volt_dev, npol: int, nsub: int, nsamp: int, nfft: int, out_dev
     float32 [nsub*nfft][out_pitch] (descending frequency within each subband)."""
     _check(load().dd_channelise(_ptr(volt_dev), int(npol), int(nsub), int(nsamp), int(nfft), _ptr(out_dev),
                                 int(out_pitch), _stream(stream)))
+
+
+# ------------------------------------------------------------------ candidate clustering
+
+def dd_cluster_candidates(cands: np.ndarray, dm_link: int, t_link: int):
+    """Friends-of-friends clusters of a candidate array (CANDIDATE_DTYPE).
+    Returns (clusters CLUSTER_DTYPE sorted by strongest member, labels [n])."""
+    c = np.ascontiguousarray(cands, dtype=CANDIDATE_DTYPE)
+    n = len(c)
+    out = np.zeros(max(n, 1), dtype=CLUSTER_DTYPE)
+    labels = np.zeros(max(n, 1), dtype=np.int64)
+    m = C.c_int64()
+    _check(load().dd_cluster_candidates(c.ctypes.data if n else None, n, int(dm_link), int(t_link),
+                                        out.ctypes.data, n, C.byref(m), labels.ctypes.data))
+    return out[:m.value].copy(), labels[:n].copy()
