@@ -45,6 +45,32 @@ TILE_CONFIGS = {0: (2, 36, 4, 8), 1: (2, 20, 4, 12), 2: (2, 28, 4, 8), 3: (3, 16
                 8: (4, 12, 8, 8)}
 
 
+# ------------------------------------------------------------------ replicas (N > 1)
+# Under torchrun each rank is an independent replica: its own beam of the
+# workload's shape (its own seed), no data-path collective; the step time is
+# the maximum over ranks and the value counts every rank's units.
+
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Seed of rank `rank`'s beam (distinct per rank)."""
+    return base_seed + 1000 * rank
+
+
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """Maximum of x over the ranks of the default process group (x if alone)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Units per second of the whole job: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def _pulses(wl, nout, seed):
     return synth.draw_pulses(16, 0.0, wl.dm_list[-1], 1, 32, 8.0, 20.0, nout - 32, wl.nchans, seed)
 
@@ -202,8 +228,8 @@ def run_ours(args, rank, world, local_rank):
         plan.set_kernel(args.kernel)
     nout, M = plan.nsamp_out, plan.maxshift
     # input: seeded noise + 16 pulses placed with the plan's own delay law
-    x = synth.noise_f32(wl.nchans, wl.nsamp, seed=wl.seed + 1000 * rank)
-    pulses = _pulses(wl, nout, seed=wl.seed + 1000 * rank)
+    x = synth.noise_f32(wl.nchans, wl.nsamp, seed=replica_seed(wl.seed, rank))
+    pulses = _pulses(wl, nout, seed=replica_seed(wl.seed, rank))
     pplan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, [p.dm for p in pulses], [1], 6.0,
                     dd.DD_F32, wl.nsamp)
     ptab = pplan.delays().astype(np.int64)
@@ -247,13 +273,10 @@ def run_ours(args, rank, world, local_rank):
         dist.barrier()
     total_ms = g0.elapsed_time(g1)
     ker_ms = statistics.mean(a.elapsed_time(b) for a, b in ev_steps)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, "cuda")
     ms_per_step = total_ms / args.steps
     units_per_rank = wl.ndm * nout
-    value = units_per_rank * world / (ms_per_step / 1e3)
+    value = whole_job_rate(units_per_rank, world, ms_per_step / 1e3)
 
     # end to end through the C ABI with host input (H2D + execute + search + readback)
     pinned = host.pin_memory()
@@ -265,8 +288,8 @@ def run_ours(args, rank, world, local_rank):
         e0 = time.perf_counter()
         c2, n2 = plan.process_host(pinned, wl.nsamp, capacity=1 << 16, stream=stream)
         e2e_t.append(time.perf_counter() - e0)
-    e2e_s = statistics.median(e2e_t)
-    e2e_value = units_per_rank * world / e2e_s
+    e2e_s = max_over_ranks(statistics.median(e2e_t), world, "cuda")
+    e2e_value = whole_job_rate(units_per_rank, world, e2e_s)
 
     kernel_id = plan.kernel
     tile = plan.tile if kernel_id in (2, 3, 4) else None
