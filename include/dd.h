@@ -306,6 +306,18 @@ DD_API int dd_server_add_beam(dd_server *server, int32_t nchans, double fch1_mhz
  * any) finishes.  Queued chunks of the beam are dropped. */
 DD_API int dd_server_remove_beam(dd_server *server, int32_t beam);
 
+/* Search variant for streaming beams: on = 1 also tests, for every searched
+ * chunk after the first, the boxcars that start in the previous chunk's last
+ * wmax - 1 outputs and end in this chunk (wmax = the beam's widest boxcar;
+ * by default windows never cross a chunk boundary).  They are tested against
+ * this chunk's thresholds (the chunk holding the window's last sample) and
+ * reported among this chunk's candidates with t < 0: the window starts |t|
+ * samples before the chunk's first output.  Keeps ndm x (wmax - 1) outputs
+ * per beam on the device (not counted against the admission budget).  Set it
+ * before the beam's first chunk; DD_ERR_ARG otherwise or if wmax - 1 >
+ * chunk. */
+DD_API int dd_server_set_boundary_search(dd_server *server, int32_t beam, int32_t on);
+
 /* Queue one chunk: chunk_host holds nchans rows of `chunk` samples,
  * host_pitch elements apart (pinned or pageable).  It must stay valid and
  * unchanged until dd_server_poll reports the chunk.  Returns immediately. */

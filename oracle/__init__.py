@@ -19,6 +19,7 @@ Paper passages followed (Magro et al. 2011):
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -375,3 +376,36 @@ def cluster(cands: np.ndarray, dm_link: int, t_link: int):
         out.append((best, sorted(members), (min(dms), max(dms)), (min(ts), max(ts))))
     out.sort(key=lambda g: key(g[0]))
     return out
+
+
+def search_stream(chunks, widths, k: float, carry: bool = True):
+    """Streaming search (serving; search variant with boundary carry): each
+    chunk's outputs [ndm][chunk] are searched with the chunk's own mu, sigma;
+    with `carry`, windows that start in the previous chunk's last wmax - 1
+    outputs and end in this chunk are also tested, against this chunk's
+    thresholds, and reported with t = start - chunk_start < 0.  Returns one
+    candidate array per chunk, sorted by (dm, t, width_idx)."""
+    widths = list(widths)
+    L = max(widths) - 1
+    res = []
+    for c, cur in enumerate(chunks):
+        cur = np.ascontiguousarray(cur)
+        mu, sg = stats(cur)
+        part = [search(cur, widths, mu, sg, k)]
+        if carry and c > 0 and L > 0:
+            prev = np.ascontiguousarray(chunks[c - 1])
+            isint = cur.dtype == np.int64
+            rows = []
+            for j in range(cur.shape[0]):
+                x = np.concatenate([prev[j, -L:], cur[j, :L]])
+                for p, w in enumerate(widths):
+                    for i in range(max(0, L - w + 1), L):
+                        b = int(np.sum(x[i:i + w])) if isint else float(np.sum(x[i:i + w], dtype=np.float64))
+                        if b > threshold(w, mu, sg, k):
+                            rows.append((j, i - L, p, (b - w * mu) / (sg * math.sqrt(w)), float(b)))
+            extra = np.array(rows, dtype=CAND_DTYPE) if rows else np.empty(0, CAND_DTYPE)
+            part.append(extra)
+        allc = np.concatenate(part)
+        order = np.lexsort((allc["width_idx"], allc["t"], allc["dm_idx"]))
+        res.append(allc[order])
+    return res

@@ -120,6 +120,10 @@ int generic_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaSt
 int stats_from_out(dd_plan *p, const void *out, cudaStream_t s);
 int search_launch(dd_plan *p, const void *out, cudaStream_t s);
 int ensure_partials_public(dd_plan *p, int64_t n);
+// windows crossing from the previous chunk (`tail`: [ndm][L] outputs) into
+// `out`, against the plan's current thresholds; hits in the plan's candidate
+// buffer (read back with search_readback)
+int boundary_search_launch(dd_plan *p, const void *tail, const void *out, int L, cudaStream_t s);
 long long max_delay(int nchans, double fch1, double foff, double tsamp_s, const double *dm_list, int ndm);
 int search_readback(dd_plan *plan, dd_candidate *cand_host, int64_t capacity, int64_t *n_found,
                     cudaStream_t s, int64_t dev_cap);

@@ -572,6 +572,68 @@ static void launch_search_pow2_k(int K, dim3 grid, cudaStream_t s, const void *o
     }
 }
 
+// Boxcars that cross a chunk boundary (streaming search variant): per DM row,
+// x = [the previous chunk's last L outputs | this chunk's first L outputs],
+// L = wmax - 1; every window of width w starting at i in [L - w + 1, L) (it
+// starts in the previous chunk and ends in this one) is tested against this
+// chunk's thresholds.  Hits get t = i - L < 0: the window starts |t| samples
+// before this chunk's first output.  S/N is formed on the host.
+template <bool kInt>
+__global__ void __launch_bounds__(128)
+boundary_search_kernel(const void *__restrict__ tail_, const void *__restrict__ out_, int64_t nout, int L,
+                       const int32_t *__restrict__ widths, int nw, const SearchParams *__restrict__ prm,
+                       const RowParams *__restrict__ rp, dd_candidate *__restrict__ cands, int64_t cap,
+                       unsigned long long *__restrict__ count)
+{
+    using T = typename std::conditional<kInt, int32_t, float>::type;
+    using Acc = typename std::conditional<kInt, long long, float>::type;
+    extern __shared__ __align__(16) unsigned char sraw[];
+    T *x = reinterpret_cast<T *>(sraw);
+    const int row = blockIdx.x;
+    const T *tail = reinterpret_cast<const T *>(tail_) + (size_t)row * L;
+    const T *head = reinterpret_cast<const T *>(out_) + (size_t)row * nout;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) { x[i] = tail[i]; x[L + i] = head[i]; }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nw * L; q += blockDim.x) {
+        const int p = q / L, i = q - p * L, w = widths[p];
+        if (i < L - w + 1) continue;                 // window ends before this chunk
+        Acc b = 0;
+        for (int j = 0; j < w; ++j) b += (Acc)x[i + j];
+        bool hit;
+        if constexpr (kInt) hit = (long long)b > (rp ? rp[row].thr_i[p] : prm->thr_i[p]);
+        else hit = b > (rp ? rp[row].thr_f[p] : prm->thr_f[p]);
+        if (hit) {
+            const unsigned long long pos = atomicAdd(count, 1ull);
+            if ((int64_t)pos < cap) {
+                dd_candidate c;
+                c.dm_idx = row; c.width_idx = p; c.t = (int64_t)i - L;
+                c.snr = 0.f; c.reserved = 0.f; c.value = (double)b;
+                cands[pos] = c;
+            }
+        }
+    }
+}
+
+int boundary_search_launch(dd_plan *p, const void *tail, const void *out, int L, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(p->d_count, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_fail(e, "memset count");
+    const int32_t *w_orig = p->d_wsorted + 2 * p->nwidths;
+    const RowParams *rp = p->row_stats ? p->d_rowprm : nullptr;
+    const size_t smem = (size_t)2 * L * 4;
+    if (p->dtype == DD_U8)
+        boundary_search_kernel<true><<<(unsigned)p->ndm, 128, smem, s>>>(tail, out, p->nsamp_out, L, w_orig, p->nwidths,
+                                                                        p->d_params, rp, p->d_cands, p->cand_cap,
+                                                                        p->d_count);
+    else
+        boundary_search_kernel<false><<<(unsigned)p->ndm, 128, smem, s>>>(tail, out, p->nsamp_out, L, w_orig,
+                                                                         p->nwidths, p->d_params, rp, p->d_cands,
+                                                                         p->cand_cap, p->d_count);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "launch boundary_search_kernel");
+    return DD_OK;
+}
+
 // S/N of the compacted hits: (B_w - w*mu) / (sigma*sqrt(w)), in double.
 __global__ void cand_snr_kernel(dd_candidate *__restrict__ cands, const unsigned long long *__restrict__ count,
                                 int64_t cap, const int32_t *__restrict__ widths, const SearchParams *__restrict__ prm,

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -42,6 +43,10 @@ struct ServerBeam {
     void *ring[2] = {nullptr, nullptr};
     int cur = 0;
     void *out = nullptr;
+    // boundary search (optional): the previous chunk's last L outputs per row
+    bool carry = false, tail_valid = false;
+    int L = 0;
+    void *tail = nullptr;
     int64_t processed = 0;
     bool busy = false, removed = false;
     std::deque<Pending> queue;
@@ -73,6 +78,7 @@ static void free_beam(ServerBeam *b)
     for (void *r : b->ring)
         if (r) cudaFree(r);
     if (b->out) cudaFree(b->out);
+    if (b->tail) cudaFree(b->tail);
     delete b;
 }
 
@@ -120,9 +126,49 @@ static void process(dd_server *S, ServerBeam *b, const Pending &pc, cudaStream_t
         found.resize((size_t)S->cand_cap);
         if (rc == DD_OK) rc = dd_search(b->plan, b->out, found.data(), S->cand_cap, &n, s);
         found.resize((size_t)std::min(n, S->cand_cap));
+        dd_last_stats(b->plan, &r.mu, &r.sigma);
+        if ((rc == DD_OK || rc == DD_ERR_OVERFLOW) && b->carry && b->L > 0) {
+            int rc2 = DD_OK;
+            if (b->tail_valid) {
+                // windows from the previous chunk's tail into this chunk
+                std::vector<dd_candidate> bnd((size_t)S->cand_cap);
+                int64_t nb = 0;
+                rc2 = boundary_search_launch(b->plan, b->tail, b->out, b->L, s);
+                if (rc2 == DD_OK)
+                    rc2 = search_readback(b->plan, bnd.data(), S->cand_cap, &nb, s, b->plan->cand_cap);
+                if (rc2 == DD_OK || rc2 == DD_ERR_OVERFLOW) {
+                    const dd_plan *p = b->plan;
+                    for (int64_t i = 0; i < std::min(nb, S->cand_cap); ++i) {
+                        dd_candidate c = bnd[(size_t)i];
+                        const double w = (double)p->widths[c.width_idx];
+                        const double mu = p->row_stats ? p->h_rowprm[c.dm_idx].mu : r.mu;
+                        const double sg = p->row_stats ? p->h_rowprm[c.dm_idx].sigma : r.sigma;
+                        c.snr = (float)((c.value - w * mu) / (sg * std::sqrt(w)));
+                        if ((int64_t)found.size() < S->cand_cap) found.push_back(c);
+                    }
+                    n += nb;
+                    std::sort(found.begin(), found.end(), [](const dd_candidate &x, const dd_candidate &y) {
+                        if (x.dm_idx != y.dm_idx) return x.dm_idx < y.dm_idx;
+                        if (x.t != y.t) return x.t < y.t;
+                        return x.width_idx < y.width_idx;
+                    });
+                    if (n > S->cand_cap) rc = DD_ERR_OVERFLOW;
+                    rc2 = DD_OK;
+                }
+            }
+            // this chunk's last L outputs of every row become the next tail
+            if (rc2 == DD_OK) {
+                cudaError_t e2 = cudaMemcpy2DAsync(b->tail, (size_t)b->L * 4, (const char *)b->out + (size_t)(b->chunk - b->L) * 4,
+                                                   (size_t)b->chunk * 4, (size_t)b->L * 4, (size_t)b->plan->ndm,
+                                                   cudaMemcpyDeviceToDevice, s);
+                if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(s);
+                if (e2 != cudaSuccess) rc2 = cuda_fail(e2, "boundary tail");
+                b->tail_valid = rc2 == DD_OK;
+            }
+            if (rc2 != DD_OK) rc = rc2;
+        }
         r.status = rc;
         r.n_candidates = n;
-        dd_last_stats(b->plan, &r.mu, &r.sigma);
     }
     b->cur = nxt;
     b->processed++;
@@ -247,6 +293,30 @@ int dd_server_add_beam(dd_server *S, int32_t nchans, double fch1, double foff, d
     b->id = S->next_id++;
     S->beams[b->id] = b;
     *beam_id = b->id;
+    return DD_OK;
+}
+
+int dd_server_set_boundary_search(dd_server *S, int32_t beam, int32_t on)
+{
+    if (!S) return set_error(DD_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->beams.find(beam);
+    if (it == S->beams.end() || it->second->removed) return set_error(DD_ERR_ARG, "no beam %d", beam);
+    ServerBeam *b = it->second;
+    if (b->busy || !b->queue.empty() || b->processed > 0)
+        return set_error(DD_ERR_ARG, "set the boundary search before the beam's first chunk");
+    int wmax = 1;
+    for (int w : b->plan->widths) wmax = std::max(wmax, w);
+    const int L = wmax - 1;
+    if (on && L > b->chunk) return set_error(DD_ERR_ARG, "widest boxcar exceeds chunk + 1");
+    if (on && L > 0 && !b->tail) {
+        cudaSetDevice(S->device);
+        cudaError_t e = cudaMalloc(&b->tail, (size_t)b->plan->ndm * L * 4);
+        if (e != cudaSuccess) { b->tail = nullptr; return cuda_fail(e, "boundary tail"); }
+    }
+    b->carry = on != 0;
+    b->L = L;
+    b->tail_valid = false;
     return DD_OK;
 }
 

@@ -37,7 +37,8 @@ EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "d
            "dd_subband_plan_info", "dd_subband_execute", "dd_subband_search", "dd_subband_last_stats",
            "dd_survey_plan_create", "dd_survey_plan_destroy", "dd_survey_pass_info", "dd_survey_execute",
            "dd_survey_search", "dd_survey_last_stats", "dd_channelise",
-           "dd_plan_set_search_stats", "dd_last_row_stats", "dd_cluster_candidates")
+           "dd_plan_set_search_stats", "dd_last_row_stats", "dd_cluster_candidates",
+           "dd_server_set_boundary_search")
 
 DD_PRIMING = 7
 
@@ -129,6 +130,7 @@ def load(path: Optional[str] = None):
             "dd_channelise": (C.c_int, [vp, i32, i32, i64, i32, vp, i64, vp]),
             "dd_plan_set_search_stats": (C.c_int, [vp, i32]),
             "dd_cluster_candidates": (C.c_int, [vp, i64, i32, i64, vp, i64, P64, vp]),
+            "dd_server_set_boundary_search": (C.c_int, [vp, i32, i32]),
             "dd_last_row_stats": (C.c_int, [vp, vp, vp]),
             "dd_last_error": (C.c_char_p, []),
             "dd_version": (C.c_char_p, []),
@@ -352,6 +354,10 @@ class Server:
 
     def remove_beam(self, beam: int) -> None:
         _check(load().dd_server_remove_beam(self.handle, int(beam)))
+
+    def set_boundary_search(self, beam: int, on: bool = True) -> None:
+        """Also search boxcars crossing from the previous chunk (reported with t < 0)."""
+        _check(load().dd_server_set_boundary_search(self.handle, int(beam), 1 if on else 0))
 
     def submit(self, beam: int, chunk_host, host_pitch: int, seq: int) -> None:
         """chunk_host must stay alive and unchanged until poll() reports (beam, seq)."""

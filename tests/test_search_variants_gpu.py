@@ -76,3 +76,78 @@ def test_per_row_statistics_match_oracle(dtype, widths):
     mu_all, sg_all = oracle.stats(ora)
     assert abs(mu - mu_all) <= max(tol_mu * max(1.0, abs(mu_all)), 1e-9)
     plan.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_server_boundary_search_matches_oracle(dtype):
+    # a beam streamed in 512-sample chunks with a pulse straddling a chunk
+    # boundary; per searched chunk: in-chunk and boundary candidates against
+    # the oracle's streaming search (gray-zone rule)
+    nch, fch1, foff, tsamp = 64, 150.0, -0.390625, 327.68e-6
+    dms = [0.1 * i for i in range(40)]
+    widths = (1, 2, 4, 8, 16)
+    chunk, K = 512, 9
+    d, M = oracle.delays(nch, fch1, foff, tsamp, dms)
+    total = K * chunk
+    x = synth.noise_f32(nch, total, 21)
+    nprime = (M + chunk - 1) // chunk
+    # stream time of the first output of chunk k is k*chunk - M; put the pulse
+    # across the boundary between searched chunks nprime+2 and nprime+3
+    tb = (nprime + 3) * chunk - M
+    synth.inject_pulses(x, [synth.Pulse(dm=dms[20], t0=tb - 5, width=10, amp=1.2)],
+                        lambda dm: oracle.delays(nch, fch1, foff, tsamp, [dm])[0][0], total)
+    if dtype == "u8":
+        x = synth.quantize_u8(x)
+    srv = dd.Server(1 << 30, nworkers=1)
+    bid = srv.add_beam(nch, fch1, foff, tsamp, dms, widths, 5.0, dd.DD_U8 if dtype == "u8" else dd.DD_F32, chunk)
+    srv.set_boundary_search(bid, True)
+    got = {}
+    for k in range(K):
+        ck = torch.from_numpy(np.ascontiguousarray(x[:, k * chunk:(k + 1) * chunk])).pin_memory()
+        srv.submit(bid, ck, chunk, k)
+        r = None
+        for _ in range(300):
+            hit = [q for q in srv.poll(wait_ms=50) if q["seq"] == k]
+            if hit:
+                r = hit[0]
+                break
+        assert r is not None and r["status"] in (0, dd.DD_PRIMING)
+        if r["status"] == 0:
+            got[k] = (srv.candidates(bid, k), r["mu"], r["sigma"])
+    ora_full = oracle.dedisperse(x, d, total - M)
+    ks = sorted(got)
+    assert ks[0] == nprime
+    chunks = [ora_full[:, k * chunk - M:(k + 1) * chunk - M] for k in ks]
+    ora = oracle.search_stream(chunks, widths, 5.0, carry=True)
+    eps = 0.0 if dtype == "u8" else fp_tol(nch)
+    L = max(widths) - 1
+    crossing = 0
+    for ci, k in enumerate(ks):
+        g, mu_g, sg_g = got[k]
+        mu_o, sg_o = oracle.stats(chunks[ci])
+        inside = g[g["t"] >= 0]
+        res = compare_candidates(inside, chunks[ci], list(widths), mu_g, sg_g, mu_o, sg_o, 5.0, eps)
+        assert res[1] <= 2
+        gb = {(int(c["dm_idx"]), int(c["t"]), int(c["width_idx"])) for c in g if c["t"] < 0}
+        ob = {(int(c["dm_idx"]), int(c["t"]), int(c["width_idx"])): float(c["value"]) for c in ora[ci] if c["t"] < 0}
+        if ci == 0:
+            assert not gb                              # no previous searched chunk
+            continue
+        prev = chunks[ci - 1]
+        for j in range(len(dms)):
+            xx = np.concatenate([prev[j, -L:], chunks[ci][j, :L]])
+            for p, w in enumerate(widths):
+                for i in range(max(0, L - w + 1), L):
+                    b = float(np.sum(xx[i:i + w]))
+                    T = oracle.threshold(w, mu_o, sg_o, 5.0)
+                    key = (j, i - L, p)
+                    if abs(b - T) <= w * eps + abs(w * (mu_g - mu_o)) + 5.0 * abs(sg_g - sg_o) * np.sqrt(w) + 1e-9:
+                        continue                       # gray zone
+                    assert (key in gb) == (b > T), (k, key, b, T)
+                    assert (key in ob) == (b > T)
+        crossing += len(gb)
+        for c in g[g["t"] < 0]:                        # S/N of boundary candidates
+            w = widths[int(c["width_idx"])]
+            assert abs(float(c["snr"]) - (float(c["value"]) - w * mu_g) / (sg_g * np.sqrt(w))) <= 1e-4
+    assert crossing > 0
+    srv.close()

@@ -38,3 +38,37 @@ def test_row_offset_and_scale_invariance():
     # the whole-buffer search is not invariant: the shifted row dominates
     mu, sg = oracle.stats(moved)
     assert _keys(oracle.search(moved, [1, 2, 4, 16], mu, sg, 4.0)) != _keys(c0)
+
+
+def test_stream_carry_tests_every_window_once():
+    # with the threshold at -inf every window of the concatenated stream is a
+    # candidate, found exactly once: N - w + 1 per row and width
+    r = np.random.default_rng(3)
+    x = r.standard_normal((3, 4 * 64))
+    chunks = [x[:, c * 64:(c + 1) * 64] for c in range(4)]
+    widths = [1, 2, 5, 16]
+    res = oracle.search_stream(chunks, widths, -1e9, carry=True)
+    n = {}
+    for c, cc in enumerate(res):
+        for row in cc:
+            start = c * 64 + int(row["t"])
+            key = (int(row["dm_idx"]), start, int(row["width_idx"]))
+            n[key] = n.get(key, 0) + 1
+    assert all(v == 1 for v in n.values())
+    for p, w in enumerate(widths):
+        for j in range(3):
+            assert sum(1 for (jj, s, pp) in n if jj == j and pp == p) == 4 * 64 - w + 1
+    # without the carry: the per-chunk search
+    res0 = oracle.search_stream(chunks, widths, -1e9, carry=False)
+    assert all(len(a) == 3 * sum(64 - w + 1 for w in widths) for a in res0)
+
+
+def test_stream_carry_finds_a_pulse_on_the_boundary():
+    r = np.random.default_rng(4)
+    x = r.standard_normal((2, 256))
+    x[1, 124:132] += 3.0                       # 8 samples straddling the boundary at 128
+    chunks = [x[:, :128], x[:, 128:]]
+    with_c = oracle.search_stream(chunks, [1, 2, 4, 8], 6.0, carry=True)[1]
+    without = oracle.search_stream(chunks, [1, 2, 4, 8], 6.0, carry=False)[1]
+    hit = [(int(c["dm_idx"]), int(c["t"]), int(c["width_idx"])) for c in with_c]
+    assert (1, -4, 3) in hit and all(int(c["t"]) >= 0 for c in without)
