@@ -4,6 +4,7 @@
 #include "dd_fast_impl.cuh"
 #include "dd_lane_impl.cuh"
 #include "dd_tmem_impl.cuh"
+#include "dd_share_impl.cuh"
 
 #include <algorithm>
 #include <climits>
@@ -11,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <array>
 
 namespace dd {
 
@@ -46,15 +48,26 @@ struct TmemCfgData {
     int32_t *d_base = nullptr;   // [nblk][nchans] row start relative to the tile start
 };
 
+struct ShareCfgData {
+    bool ok = false;
+    int nblk = 0, nsub = 0, rs = 0, pmax = 0, bar_off = 0;
+    size_t smem = 0;
+    int32_t *d_rec = nullptr;    // [nblk][nsub][kLen] subband records
+    int32_t *d_base = nullptr;   // [nblk][nchans] staged row starts
+};
+
 // Tile configurations: indices [0, kNumFastCfg) are kernel 2 shapes,
-// [kNumFastCfg, kLaneEnd) kernel 3 shapes, [kLaneEnd, kNumAllCfg) kernel 4.
+// [kNumFastCfg, kLaneEnd) kernel 3 shapes, [kLaneEnd, kShareCfg) kernel 4,
+// kShareCfg kernel 5.
 constexpr int kLaneEnd = kNumFastCfg + kNumLaneCfg;
-constexpr int kNumAllCfg = kLaneEnd + kNumTmemCfg;
+constexpr int kShareCfg = kLaneEnd + kNumTmemCfg;
+constexpr int kNumAllCfg = kShareCfg + 1;
 
 struct FastPlan {
     FastCfgData cfg[kNumFastCfg];
     LaneCfgData lane[kNumLaneCfg];
     TmemCfgData tm[kNumTmemCfg];
+    ShareCfgData sh;
     int active = -1;
     int dgroup = 8;
     int al = 4;                  // row alignment in elements (16 bytes)
@@ -233,6 +246,104 @@ static int build_tmem(const dd_plan *p, int n, int dbw, int nw, TmemCfgData &c)
     return DD_OK;
 }
 
+static void free_share(ShareCfgData &c)
+{
+    if (c.d_rec) cudaFree(c.d_rec);
+    if (c.d_base) cudaFree(c.d_base);
+    c.d_rec = nullptr; c.d_base = nullptr;
+    c.ok = false;
+}
+
+// Kernel 5 tables.  Per (DM block, subband of kShCS channels): the trials'
+// relative delays r(c) = d(c,dm) - d(ref,dm) (ref = the subband's highest
+// frequency) grouped into patterns; per pattern the range of P samples its
+// trials need and where they sit in the packed P buffer; per trial the index
+// of its t = t0 term.  c.ok stays false when the channel count is not a
+// multiple of kShCS, a (block, subband) has more than kShNP patterns, or the
+// buffers do not fit three blocks per SM.
+static int build_share(const dd_plan *p, ShareCfgData &c)
+{
+    c = ShareCfgData();
+    constexpr int CS = kShCS, DB = kShDR * kShNW, NP = kShNP, TILE = 32 * kShTI;
+    using R = ShareRecC;
+    const int C = p->nchans, D = p->ndm;
+    if (C % CS) return DD_OK;
+    const int S = C / CS, nblk = (D + DB - 1) / DB;
+    const int AL = elem_align(p->dtype);
+    std::vector<int32_t> rec((size_t)nblk * S * R::kLen, 0), base((size_t)nblk * C);
+    auto dl = [&](int dm, int ch) { return p->delays[(size_t)std::min(dm, D - 1) * C + ch]; };
+    long long need = 0;
+    int pmax = 0;
+    for (int b = 0; b < nblk; ++b)
+        for (int s = 0; s < S; ++s) {
+            const int ref = p->foff < 0.0 ? s * CS : s * CS + CS - 1;
+            int dref[DB], pid[DB];
+            std::vector<std::array<int, CS>> pats;
+            int dmin = INT_MAX;
+            for (int j = 0; j < DB; ++j) {
+                dref[j] = dl(b * DB + j, ref);
+                dmin = std::min(dmin, dref[j]);
+                std::array<int, CS> r;
+                for (int cc = 0; cc < CS; ++cc) r[cc] = dl(b * DB + j, s * CS + cc) - dref[j];
+                int k = 0;
+                while (k < (int)pats.size() && pats[k] != r) ++k;
+                if (k == (int)pats.size()) pats.push_back(r);
+                pid[j] = k;
+            }
+            if ((int)pats.size() > NP) return DD_OK;
+            int32_t *t = &rec[((size_t)b * S + s) * R::kLen];
+            t[R::kNpat] = (int32_t)pats.size();
+            for (int cc = 0; cc < CS; ++cc) {
+                int lo = INT_MAX, hi = 0;
+                for (int j = 0; j < DB; ++j) {
+                    const int d = dl(b * DB + j, s * CS + cc);
+                    lo = std::min(lo, d); hi = std::max(hi, d);
+                }
+                const int b0 = lo - (lo % AL);
+                base[(size_t)b * C + s * CS + cc] = b0;
+                t[R::kRowoff + cc] = dmin - b0;
+                need = std::max<long long>(need, (long long)(hi - b0) + TILE);
+            }
+            int poff = 0;
+            std::vector<int> plo(pats.size());
+            for (int k = 0; k < (int)pats.size(); ++k) {
+                int lo = INT_MAX, hi = INT_MIN;
+                for (int j = 0; j < DB; ++j)
+                    if (pid[j] == k) { lo = std::min(lo, dref[j] - dmin); hi = std::max(hi, dref[j] - dmin); }
+                const int W = hi - lo + TILE;
+                int32_t *pr = t + R::kPat + k * R::kPatLen;
+                pr[0] = poff; pr[1] = lo; pr[2] = W;
+                for (int cc = 0; cc < CS; ++cc) pr[3 + cc] = pats[k][cc];
+                plo[k] = lo;
+                poff += W;
+            }
+            poff = 0;
+            std::vector<int> pof(pats.size());
+            for (int k = 0; k < (int)pats.size(); ++k) { pof[k] = poff; poff += t[R::kPat + k * R::kPatLen + 2]; }
+            pmax = std::max(pmax, poff);
+            for (int j = 0; j < DB; ++j) t[R::kTrial + j] = pof[pid[j]] + (dref[j] - dmin - plo[pid[j]]);
+        }
+    const int rs = (int)((need + 15) / 16 * 16);
+    const size_t eb = in_elem_bytes(p->dtype);
+    // three blocks per SM if the buffers fit, else two
+    const size_t rows_b = (size_t)kShStages * CS * rs * eb, rec_b = (size_t)kShStages * R::kLen * 4;
+    const size_t p_b = (size_t)2 * ((pmax + 3) / 4 * 4) * 4;
+    const size_t bar_off = (rows_b + rec_b + p_b + 15) / 16 * 16;
+    const size_t need_b = bar_off + kShStages * sizeof(uint64_t);
+    const size_t budget3 = std::min<size_t>(p->smem_optin, (228 * 1024) / 3 - 1024) - 1024;
+    const size_t budget2 = std::min<size_t>(p->smem_optin, (228 * 1024) / 2 - 1024) - 1024;
+    if (need_b > budget3 && need_b > budget2) return DD_OK;
+    c.nblk = nblk; c.nsub = S; c.rs = rs; c.pmax = (pmax + 3) / 4 * 4; c.bar_off = (int)bar_off;
+    c.smem = need_b;
+    cudaError_t e = cudaMalloc(&c.d_rec, rec.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_base, base.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_rec, rec.data(), rec.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { free_share(c); return cuda_fail(e, "kernel 5 tables"); }
+    c.ok = true;
+    return DD_OK;
+}
+
 static void free_cfg(FastCfgData &c)
 {
     if (c.d_desc) cudaFree(c.d_desc);
@@ -344,7 +455,8 @@ static bool cfg_ok(const FastPlan *f, int k)
 {
     if (k < 0 || k >= kNumAllCfg) return false;
     if (k < kNumFastCfg) return f->cfg[k].ok;
-    return k < kLaneEnd ? f->lane[k - kNumFastCfg].ok : f->tm[k - kLaneEnd].ok;
+    if (k < kLaneEnd) return f->lane[k - kNumFastCfg].ok;
+    return k < kShareCfg ? f->tm[k - kLaneEnd].ok : f->sh.ok;
 }
 
 int fast_configure(dd_plan *p)
@@ -359,6 +471,7 @@ int fast_configure(dd_plan *p)
         rc = build_lane(p, kLaneCfg[k].ti, kLaneCfg[k].dr, kLaneCfg[k].nw, kLaneCfg[k].minb, f->lane[k]);
     for (int k = 0; k < kNumTmemCfg && rc == DD_OK; ++k)
         rc = build_tmem(p, kTmemCfg[k].n, kTmemCfg[k].dbw, kTmemCfg[k].nw, f->tm[k]);
+    if (rc == DD_OK) rc = build_share(p, f->sh);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < kNumFastCfg && rc == DD_OK && e == cudaSuccess; ++k)
         if (f->cfg[k].ok) e = prepare_cfg(k, p->smem_optin);
@@ -366,6 +479,7 @@ int fast_configure(dd_plan *p)
         if (f->lane[k].ok) e = prepare_lane(k, p->smem_optin);
     for (int k = 0; k < kNumTmemCfg && rc == DD_OK && e == cudaSuccess; ++k)
         if (f->tm[k].ok) e = prepare_tmem(k, p->smem_optin);
+    if (rc == DD_OK && e == cudaSuccess && f->sh.ok) e = share_prepare(p->smem_optin);
     if (rc == DD_OK && e == cudaSuccess) e = cudaMalloc(&f->d_err, sizeof(int));
     if (rc == DD_OK && e == cudaSuccess) e = cudaMemset(f->d_err, 0, sizeof(int));
     p->fast = f;
@@ -451,8 +565,34 @@ static int tmem_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch
     return DD_OK;
 }
 
+static int share_run(dd_plan *p, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s)
+{
+    FastPlan *f = static_cast<FastPlan *>(p->fast);
+    ShareCfgData &c = f->sh;
+    const int tile = 32 * kShTI;
+    const int64_t ntile = (p->nsamp_out + tile - 1) / tile;
+    if (ntile * c.nblk > INT32_MAX) return generic_execute(p, in, pitch, out, s);
+    const int64_t np = ntile * c.nblk;
+    int rc = ensure_partials_public(p, np);
+    if (rc) return rc;
+    ShareLaunch a;
+    a.in = in; a.pitch = pitch;
+    a.nsamp_in_al = (p->nsamp_in + f->al - 1) / f->al * f->al;
+    a.nchans = p->nchans; a.ndm = p->ndm; a.nsub = c.nsub; a.nout = p->nsamp_out;
+    a.rec = c.d_rec; a.base = c.d_base;
+    a.rs = c.rs; a.pmax = c.pmax; a.bar_off = c.bar_off; a.nblk = c.nblk;
+    a.ntile = ntile; a.dgroup = std::max(1, std::min(dgroup, c.nblk));
+    a.out = out; a.partials = p->d_partials; a.err = f->d_err; a.smem = c.smem;
+    cudaError_t e = share_launch(p->dtype, a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launch share_kernel");
+    p->n_partials = np;
+    p->stats_out = out;
+    return DD_OK;
+}
+
 static int fast_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s)
 {
+    if (k == kShareCfg) return share_run(p, dgroup, in, pitch, out, s);
     if (k >= kLaneEnd) return tmem_run(p, k - kLaneEnd, dgroup, in, pitch, out, s);
     if (k >= kNumFastCfg) return lane_run(p, k - kNumFastCfg, dgroup, in, pitch, out, s);
     FastPlan *f = static_cast<FastPlan *>(p->fast);
@@ -499,9 +639,9 @@ int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStre
     int bk = f->active, bg = f->dgroup, rc = DD_OK;
     // largest raster group first: on a tie (within 0.5%) it keeps the least DRAM traffic
     const int groups[] = {16, 8, 4};
-    // kernels 2 and 3; kernel 4 (slower on every plan measured) runs only on request
-    for (int k = 0; k < kLaneEnd && rc == DD_OK; ++k) {
-        if (!cfg_ok(f, k)) continue;
+    // kernels 2, 3 and 5; kernel 4 (slower on every plan measured) runs only on request
+    for (int k = 0; k < kNumAllCfg && rc == DD_OK; ++k) {
+        if ((k >= kLaneEnd && k < kShareCfg) || !cfg_ok(f, k)) continue;
         rc = fast_run(p, k, 8, in, pitch, out, s);             // warm-up (caches, clocks)
         for (int gi = 0; gi < 3 && rc == DD_OK; ++gi) {
             cudaEventRecord(e0, s);
@@ -551,9 +691,12 @@ int fast_get_tile(const dd_plan *p, int *cfg, int *dgroup, int *tr, int *nw)
     } else if (f->active < kLaneEnd) {
         if (tr) *tr = f->lane[f->active - kNumFastCfg].ti;
         if (nw) *nw = f->lane[f->active - kNumFastCfg].nw;
-    } else {
+    } else if (f->active < kShareCfg) {
         if (tr) *tr = f->tm[f->active - kLaneEnd].n;
         if (nw) *nw = f->tm[f->active - kLaneEnd].nw;
+    } else {
+        if (tr) *tr = kShTI;
+        if (nw) *nw = kShNW;
     }
     return DD_OK;
 }
@@ -562,7 +705,8 @@ int fast_kernel_id(const dd_plan *p)
 {
     const FastPlan *f = static_cast<const FastPlan *>(p->fast);
     if (!f || f->active < kNumFastCfg) return 2;
-    return f->active < kLaneEnd ? 3 : 4;
+    if (f->active < kLaneEnd) return 3;
+    return f->active < kShareCfg ? 4 : 5;
 }
 
 void fast_release(dd_plan *p)
@@ -572,6 +716,7 @@ void fast_release(dd_plan *p)
     for (int k = 0; k < kNumFastCfg; ++k) free_cfg(f->cfg[k]);
     for (int k = 0; k < kNumLaneCfg; ++k) free_lane(f->lane[k]);
     for (int k = 0; k < kNumTmemCfg; ++k) free_tmem(f->tm[k]);
+    free_share(f->sh);
     if (f->d_err) cudaFree(f->d_err);
     delete f;
     p->fast = nullptr;

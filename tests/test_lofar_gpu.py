@@ -77,16 +77,17 @@ def test_sampled_points(lofar):
     _check_sampled(x, d, nout, out, 32 * lofar["plan"].tile[2], 123)
 
 
-@pytest.mark.parametrize("cfg", [7, 8])
+@pytest.mark.parametrize("cfg", [7, 8, 9])
 def test_kernel4_full_size(lofar, cfg):
-    # the tensor-memory kernel on the full plan: sampled points and one whole row
+    # the tensor-memory kernel (configs 7, 8) and the shared-subband kernel
+    # (config 9) on the full plan: sampled points and one whole row
     x, d, nout = lofar["x"], lofar["d"], lofar["nout"]
     wl = WL
     plan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, wl.sigma,
                    dd.DD_F32, wl.nsamp)
-    plan.set_kernel(4)
+    plan.set_kernel(4 if cfg < 9 else 5)
     plan.set_tile(cfg, 16)
-    assert plan.kernel == 4
+    assert plan.kernel == (4 if cfg < 9 else 5)
     xin = torch.from_numpy(x).cuda()
     out = torch.empty(wl.ndm * nout, dtype=torch.float32, device="cuda")
     plan.execute(xin, wl.nsamp, out)

@@ -103,7 +103,8 @@ def test_small_workload_parity(dtype, kernel):
 
 
 @pytest.mark.parametrize("tile", [(0, 1), (0, 3), (1, 8), (1, 2), (2, 16), (3, 8), (3, 1), (4, 4),
-                                  (5, 8), (5, 3), (6, 16), (6, 2), (7, 8), (7, 3), (8, 16), (8, 1)])
+                                  (5, 8), (5, 3), (6, 16), (6, 2), (7, 8), (7, 3), (8, 16), (8, 1),
+                                  (9, 8), (9, 1)])
 @pytest.mark.parametrize("dtype", ["f32", "u8", "f16"])
 def test_small_workload_tile_configs(dtype, tile):
     # every compiled tile configuration of kernels 2-4 and several raster
@@ -114,11 +115,12 @@ def test_small_workload_tile_configs(dtype, tile):
                                               wl.dm_list, wl.widths, wl.sigma, dtype, seed=wl.seed,
                                               pulses=small_pulse(), kernel=2, tile=tile)
     except dd.DDError as e:
-        # kernel 4 windows must fit the warp's TMEM buffer: config 8 (8 trials
-        # per warp) does not at this plan's ~25 samples per DM step
-        assert tile[0] == 8 and e.code == 1
+        # kernel 4 windows must fit the warp's TMEM buffer (config 8 does not
+        # at this plan's ~25 samples per DM step); kernel 5 needs at most 8
+        # delay patterns per block and 4-channel subband
+        assert tile[0] in (8, 9) and e.code == 1
         pytest.skip("configuration unavailable for this plan")
-    assert used == (2 if tile[0] < 3 else 3 if tile[0] < 7 else 4)
+    assert used == (2 if tile[0] < 3 else 3 if tile[0] < 7 else 4 if tile[0] < 9 else 5)
 
 
 @pytest.mark.parametrize("tile", [(7, 8), (8, 4), (8, 1)])
@@ -138,6 +140,22 @@ def test_kernel4_lofar_geometry(dtype, tile):
                                           6.0, dtype, seed=77, pulses=pulses, kernel=4, tile=tile,
                                           max_gray=2)
     assert used == 4
+
+
+@pytest.mark.parametrize("group", [8, 1])
+@pytest.mark.parametrize("dtype", ["f32", "u8", "f16"])
+def test_kernel5_lofar_full_band(dtype, group):
+    # the shared-subband kernel on the full LOFAR band (1024 channels: at most
+    # 7 delay patterns per 32-trial block and 4-channel subband), 100 trials
+    # (ragged last block), 2^15 samples, two pulses
+    lw = synth.workload("lofar_f32")
+    dms = [0.05 * i for i in range(100)]
+    pulses = [synth.Pulse(dm=dms[61], t0=5000, width=8, amp=0.3),
+              synth.Pulse(dm=dms[97], t0=9001, width=3, amp=0.5)]
+    cands, out, ora, res, used = run_case(lw.nchans, lw.fch1, lw.foff, lw.tsamp, (1 << 15) + 17, dms,
+                                          [1, 2, 4, 8, 16], 6.0, dtype, seed=78, pulses=pulses, kernel=5,
+                                          tile=(9, group), max_gray=2)
+    assert used == 5
 
 
 def test_autotune_keeps_parity():
@@ -187,7 +205,7 @@ def test_edge_shapes(case, dtype):
     _, m = oracle.delays(nch, fch1, foff, tsamp, dms)
     nsamp = m + extra
     pitch = nsamp + pad
-    for kernel in (0, 1, 3, 4):
+    for kernel in (0, 1, 3, 4, 5):
         try:
             run_case(nch, fch1, foff, tsamp, nsamp, dms, widths, 3.0, dtype, seed=case + 100,
                      pitch=pitch, kernel=kernel, max_gray=2)
