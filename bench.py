@@ -42,7 +42,7 @@ PROFILED_TRAFFIC = {(5, 16): 25.63e9}
 # DM trials per thread or warp, warps per block)
 TILE_CONFIGS = {0: (2, 36, 4, 8), 1: (2, 20, 4, 12), 2: (2, 28, 4, 8), 3: (3, 16, 4, 8),
                 4: (3, 16, 8, 8), 5: (3, 16, 8, 4), 6: (3, 8, 16, 4), 7: (4, 20, 4, 8),
-                8: (4, 12, 8, 8)}
+                8: (4, 12, 8, 8), 9: (5, 16, 8, 4), 10: (5, 8, 8, 4)}
 
 
 # ------------------------------------------------------------------ replicas (N > 1)
@@ -318,6 +318,12 @@ def run_ours(args, rank, world, local_rank):
             "traffic": PROFILED_TRAFFIC.get(tuple(tile[:2])) if tile else None,
             "traffic_unit": "bytes per launch",
             "kernel_ms": ker_ms}
+    if kernel_id == 5:
+        # kernel 5 shares each 4-channel subband's partial sums between the DM
+        # trials of a block with the same relative delays: `achieved` counts
+        # the brute-force-equivalent channel-adds of the exact result
+        roof["note"] = ("kernel 5: exact shared subband partial sums; achieved = brute-force-equivalent "
+                        "channel-adds (the sum is identical; fewer adds are executed)")
     if kernel_id == 3:
         # kernel 3 loads one shared-memory word per add: the shared-memory data
         # path (32 words/clk/SM, 4 B x 32 banks) caps it at a quarter of the add peak

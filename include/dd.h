@@ -179,17 +179,21 @@ DD_API int dd_process_host(dd_plan *plan, const void *in_host, int64_t in_pitch,
  * reused across 4 DM trials per thread), 3 = lane-interleaved kernel (one
  * conflict-free shared load per add, no branches), 4 = tensor-memory window
  * kernel (each staged input word copied once into TMEM and read back by every
- * DM trial of the warp at a runtime column offset).  Kernels 2-4 share the
- * tile-configuration list of dd_plan_set_tile.  Returns DD_ERR_ARG if the
- * requested kernel cannot run this plan. */
+ * DM trial of the warp at a runtime column offset), 5 = shared subband
+ * partial sums (the DM trials of a block whose delays relative to a 4-channel
+ * subband's reference coincide share that subband's partial sum: the exact
+ * brute-force result with fewer adds; needs at most 8 such delay patterns per
+ * block and subband).  Kernels 2-5 share the tile-configuration list of
+ * dd_plan_set_tile.  Returns DD_ERR_ARG if the requested kernel cannot run
+ * this plan. */
 DD_API int dd_plan_set_kernel(dd_plan *plan, int32_t kernel);
 
-/* Kernel that dd_execute will launch for this plan (1 to 4, see above). */
+/* Kernel that dd_execute will launch for this plan (1 to 5, see above). */
 DD_API int dd_plan_get_kernel(const dd_plan *plan, int32_t *kernel);
 
 /* Autotuner for the tiled kernels: runs the plan on the caller's buffers
- * once per compiled tile configuration of kernels 2 and 3 (0-6, see
- * dd_plan_set_tile) and raster group, times each with CUDA events on
+ * once per compiled tile configuration of kernels 2, 3 and 5 (0-6, 9, 10,
+ * see dd_plan_set_tile) and raster group, times each with CUDA events on
  * `stream`, keeps the fastest for this plan and caches the choice
  * process-wide for plans of the same shape.  Kernel 4 is not timed (slower on
  * every plan measured); dd_plan_set_kernel(plan, 4) selects it.  Writes
@@ -204,7 +208,9 @@ DD_API int dd_plan_autotune(dd_plan *plan, const void *in_dev, int64_t in_pitch,
  * 1: 20 x 4, 12 warps; 2: 28 x 4, 8 warps; kernel 3 (samples per lane x
  * DM trials per warp, warps) — 3: 16 x 4, 8 warps; 4: 16 x 8, 8 warps;
  * 5: 16 x 8, 4 warps; 6: 8 x 16, 4 warps; kernel 4 (samples per lane x DM
- * trials per warp, warps) — 7: 20 x 4, 8 warps; 8: 12 x 8, 8 warps};
+ * trials per warp, warps) — 7: 20 x 4, 8 warps; 8: 12 x 8, 8 warps; kernel
+ * 5 (samples per lane x DM trials per warp, warps; 4-channel subbands) — 9:
+ * 16 x 8, 4 warps; 10: 8 x 8, 4 warps};
  * raster_group (>= 1) is the number of DM blocks whose time tiles are swept
  * together.  DD_ERR_ARG if the configuration cannot run this plan. */
 DD_API int dd_plan_set_tile(dd_plan *plan, int32_t config, int32_t raster_group);

@@ -57,17 +57,17 @@ struct ShareCfgData {
 };
 
 // Tile configurations: indices [0, kNumFastCfg) are kernel 2 shapes,
-// [kNumFastCfg, kLaneEnd) kernel 3 shapes, [kLaneEnd, kShareCfg) kernel 4,
-// kShareCfg kernel 5.
+// [kNumFastCfg, kLaneEnd) kernel 3 shapes, [kLaneEnd, kShareBeg) kernel 4,
+// [kShareBeg, kNumAllCfg) kernel 5.
 constexpr int kLaneEnd = kNumFastCfg + kNumLaneCfg;
-constexpr int kShareCfg = kLaneEnd + kNumTmemCfg;
-constexpr int kNumAllCfg = kShareCfg + 1;
+constexpr int kShareBeg = kLaneEnd + kNumTmemCfg;
+constexpr int kNumAllCfg = kShareBeg + kNumShareCfg;
 
 struct FastPlan {
     FastCfgData cfg[kNumFastCfg];
     LaneCfgData lane[kNumLaneCfg];
     TmemCfgData tm[kNumTmemCfg];
-    ShareCfgData sh;
+    ShareCfgData sh[kNumShareCfg];
     int active = -1;
     int dgroup = 8;
     int al = 4;                  // row alignment in elements (16 bytes)
@@ -261,10 +261,11 @@ static void free_share(ShareCfgData &c)
 // of its t = t0 term.  c.ok stays false when the channel count is not a
 // multiple of kShCS, a (block, subband) has more than kShNP patterns, or the
 // buffers do not fit three blocks per SM.
-static int build_share(const dd_plan *p, ShareCfgData &c)
+static int build_share(const dd_plan *p, int k, ShareCfgData &c)
 {
     c = ShareCfgData();
-    constexpr int CS = kShCS, DB = kShDR * kShNW, NP = kShNP, TILE = 32 * kShTI;
+    constexpr int CS = kShCS, DB = kShDR * kShNW, NP = kShNP;
+    const int TILE = 32 * kShareCfg[k].ti, minb = kShareCfg[k].minb;
     using R = ShareRecC;
     const int C = p->nchans, D = p->ndm;
     if (C % CS) return DD_OK;
@@ -325,14 +326,15 @@ static int build_share(const dd_plan *p, ShareCfgData &c)
         }
     const int rs = (int)((need + 15) / 16 * 16);
     const size_t eb = in_elem_bytes(p->dtype);
-    // three blocks per SM if the buffers fit, else two
+    // the shape's target blocks per SM if the buffers fit, else fewer (>= 2)
     const size_t rows_b = (size_t)kShStages * CS * rs * eb, rec_b = (size_t)kShStages * R::kLen * 4;
     const size_t p_b = (size_t)2 * ((pmax + 3) / 4 * 4) * 4;
     const size_t bar_off = (rows_b + rec_b + p_b + 15) / 16 * 16;
     const size_t need_b = bar_off + kShStages * sizeof(uint64_t);
-    const size_t budget3 = std::min<size_t>(p->smem_optin, (228 * 1024) / 3 - 1024) - 1024;
-    const size_t budget2 = std::min<size_t>(p->smem_optin, (228 * 1024) / 2 - 1024) - 1024;
-    if (need_b > budget3 && need_b > budget2) return DD_OK;
+    bool fits = false;
+    for (int nb = minb; nb >= 2 && !fits; --nb)
+        fits = need_b <= std::min<size_t>(p->smem_optin, (228 * 1024) / nb - 1024) - 1024;
+    if (!fits) return DD_OK;
     c.nblk = nblk; c.nsub = S; c.rs = rs; c.pmax = (pmax + 3) / 4 * 4; c.bar_off = (int)bar_off;
     c.smem = need_b;
     cudaError_t e = cudaMalloc(&c.d_rec, rec.size() * 4);
@@ -456,7 +458,7 @@ static bool cfg_ok(const FastPlan *f, int k)
     if (k < 0 || k >= kNumAllCfg) return false;
     if (k < kNumFastCfg) return f->cfg[k].ok;
     if (k < kLaneEnd) return f->lane[k - kNumFastCfg].ok;
-    return k < kShareCfg ? f->tm[k - kLaneEnd].ok : f->sh.ok;
+    return k < kShareBeg ? f->tm[k - kLaneEnd].ok : f->sh[k - kShareBeg].ok;
 }
 
 int fast_configure(dd_plan *p)
@@ -471,7 +473,7 @@ int fast_configure(dd_plan *p)
         rc = build_lane(p, kLaneCfg[k].ti, kLaneCfg[k].dr, kLaneCfg[k].nw, kLaneCfg[k].minb, f->lane[k]);
     for (int k = 0; k < kNumTmemCfg && rc == DD_OK; ++k)
         rc = build_tmem(p, kTmemCfg[k].n, kTmemCfg[k].dbw, kTmemCfg[k].nw, f->tm[k]);
-    if (rc == DD_OK) rc = build_share(p, f->sh);
+    for (int k = 0; k < kNumShareCfg && rc == DD_OK; ++k) rc = build_share(p, k, f->sh[k]);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < kNumFastCfg && rc == DD_OK && e == cudaSuccess; ++k)
         if (f->cfg[k].ok) e = prepare_cfg(k, p->smem_optin);
@@ -479,7 +481,8 @@ int fast_configure(dd_plan *p)
         if (f->lane[k].ok) e = prepare_lane(k, p->smem_optin);
     for (int k = 0; k < kNumTmemCfg && rc == DD_OK && e == cudaSuccess; ++k)
         if (f->tm[k].ok) e = prepare_tmem(k, p->smem_optin);
-    if (rc == DD_OK && e == cudaSuccess && f->sh.ok) e = share_prepare(p->smem_optin);
+    for (int k = 0; k < kNumShareCfg && rc == DD_OK && e == cudaSuccess; ++k)
+        if (f->sh[k].ok) e = share_prepare(k, p->smem_optin);
     if (rc == DD_OK && e == cudaSuccess) e = cudaMalloc(&f->d_err, sizeof(int));
     if (rc == DD_OK && e == cudaSuccess) e = cudaMemset(f->d_err, 0, sizeof(int));
     p->fast = f;
@@ -565,11 +568,11 @@ static int tmem_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch
     return DD_OK;
 }
 
-static int share_run(dd_plan *p, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s)
+static int share_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s)
 {
     FastPlan *f = static_cast<FastPlan *>(p->fast);
-    ShareCfgData &c = f->sh;
-    const int tile = 32 * kShTI;
+    ShareCfgData &c = f->sh[k];
+    const int tile = 32 * kShareCfg[k].ti;
     const int64_t ntile = (p->nsamp_out + tile - 1) / tile;
     if (ntile * c.nblk > INT32_MAX) return generic_execute(p, in, pitch, out, s);
     const int64_t np = ntile * c.nblk;
@@ -583,7 +586,7 @@ static int share_run(dd_plan *p, int dgroup, const void *in, int64_t pitch, void
     a.rs = c.rs; a.pmax = c.pmax; a.bar_off = c.bar_off; a.nblk = c.nblk;
     a.ntile = ntile; a.dgroup = std::max(1, std::min(dgroup, c.nblk));
     a.out = out; a.partials = p->d_partials; a.err = f->d_err; a.smem = c.smem;
-    cudaError_t e = share_launch(p->dtype, a, s);
+    cudaError_t e = share_launch(k, p->dtype, a, s);
     if (e != cudaSuccess) return cuda_fail(e, "launch share_kernel");
     p->n_partials = np;
     p->stats_out = out;
@@ -592,7 +595,7 @@ static int share_run(dd_plan *p, int dgroup, const void *in, int64_t pitch, void
 
 static int fast_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s)
 {
-    if (k == kShareCfg) return share_run(p, dgroup, in, pitch, out, s);
+    if (k >= kShareBeg) return share_run(p, k - kShareBeg, dgroup, in, pitch, out, s);
     if (k >= kLaneEnd) return tmem_run(p, k - kLaneEnd, dgroup, in, pitch, out, s);
     if (k >= kNumFastCfg) return lane_run(p, k - kNumFastCfg, dgroup, in, pitch, out, s);
     FastPlan *f = static_cast<FastPlan *>(p->fast);
@@ -641,7 +644,7 @@ int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStre
     const int groups[] = {16, 8, 4};
     // kernels 2, 3 and 5; kernel 4 (slower on every plan measured) runs only on request
     for (int k = 0; k < kNumAllCfg && rc == DD_OK; ++k) {
-        if ((k >= kLaneEnd && k < kShareCfg) || !cfg_ok(f, k)) continue;
+        if ((k >= kLaneEnd && k < kShareBeg) || !cfg_ok(f, k)) continue;
         rc = fast_run(p, k, 8, in, pitch, out, s);             // warm-up (caches, clocks)
         for (int gi = 0; gi < 3 && rc == DD_OK; ++gi) {
             cudaEventRecord(e0, s);
@@ -691,11 +694,11 @@ int fast_get_tile(const dd_plan *p, int *cfg, int *dgroup, int *tr, int *nw)
     } else if (f->active < kLaneEnd) {
         if (tr) *tr = f->lane[f->active - kNumFastCfg].ti;
         if (nw) *nw = f->lane[f->active - kNumFastCfg].nw;
-    } else if (f->active < kShareCfg) {
+    } else if (f->active < kShareBeg) {
         if (tr) *tr = f->tm[f->active - kLaneEnd].n;
         if (nw) *nw = f->tm[f->active - kLaneEnd].nw;
     } else {
-        if (tr) *tr = kShTI;
+        if (tr) *tr = kShareCfg[f->active - kShareBeg].ti;
         if (nw) *nw = kShNW;
     }
     return DD_OK;
@@ -706,7 +709,7 @@ int fast_kernel_id(const dd_plan *p)
     const FastPlan *f = static_cast<const FastPlan *>(p->fast);
     if (!f || f->active < kNumFastCfg) return 2;
     if (f->active < kLaneEnd) return 3;
-    return f->active < kShareCfg ? 4 : 5;
+    return f->active < kShareBeg ? 4 : 5;
 }
 
 void fast_release(dd_plan *p)
@@ -716,7 +719,7 @@ void fast_release(dd_plan *p)
     for (int k = 0; k < kNumFastCfg; ++k) free_cfg(f->cfg[k]);
     for (int k = 0; k < kNumLaneCfg; ++k) free_lane(f->lane[k]);
     for (int k = 0; k < kNumTmemCfg; ++k) free_tmem(f->tm[k]);
-    free_share(f->sh);
+    for (int k = 0; k < kNumShareCfg; ++k) free_share(f->sh[k]);
     if (f->d_err) cudaFree(f->d_err);
     delete f;
     p->fast = nullptr;

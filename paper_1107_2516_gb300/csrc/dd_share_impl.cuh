@@ -60,8 +60,8 @@ struct ShareLaunch {
     size_t smem;
 };
 
-template <typename Tin, bool kInt, int TI, int DR, int NW, int CS, int NPMAX>
-__global__ void __launch_bounds__(NW * 32, 3) share_kernel(ShareLaunch a)
+template <typename Tin, bool kInt, int TI, int DR, int NW, int CS, int NPMAX, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
 {
     constexpr int kDmBlk = DR * NW, kT = NW * 32;
     using R = ShareRec<CS, NPMAX, kDmBlk>;
@@ -222,12 +222,16 @@ __global__ void __launch_bounds__(NW * 32, 3) share_kernel(ShareLaunch a)
     }
 }
 
-// Compiled shape: 16 samples per lane, 8 trials per warp, 4 warps, subbands
-// of 4 channels, at most 8 patterns per (block, subband).
-constexpr int kShTI = 16, kShDR = 8, kShNW = 4, kShCS = 4, kShNP = 8;
+// Compiled shapes: subbands of 4 channels, at most 8 patterns per (block,
+// subband), 8 trials per warp, 4 warps (32 trials); {samples per lane,
+// resident blocks per SM the register budget targets}.
+constexpr int kShDR = 8, kShNW = 4, kShCS = 4, kShNP = 8;
 using ShareRecC = ShareRec<kShCS, kShNP, kShDR * kShNW>;
+struct ShareShape { int ti, minb; };
+constexpr int kNumShareCfg = 2;
+constexpr ShareShape kShareCfg[kNumShareCfg] = {{16, 3}, {8, 5}};
 
-cudaError_t share_launch(dd_dtype t, const ShareLaunch &a, cudaStream_t s);
-cudaError_t share_prepare(size_t optin);
+cudaError_t share_launch(int k, dd_dtype t, const ShareLaunch &a, cudaStream_t s);
+cudaError_t share_prepare(int k, size_t optin);
 
 }  // namespace dd
