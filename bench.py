@@ -36,7 +36,7 @@ METRIC = "DM-trial·samples/s"
 WORKLOAD = "lofar_f32"
 # ncu DRAM bytes (read + write) per de-dispersion launch, keyed by the
 # (tile configuration, raster group) the capture used
-PROFILED_TRAFFIC = {(5, 16): 25.63e9}
+PROFILED_TRAFFIC = {(5, 16): 25.63e9, (9, 16): 25.62e9}
 
 # tile configurations of dd_plan_set_tile: (kernel, samples per thread or lane,
 # DM trials per thread or warp, warps per block)
@@ -292,7 +292,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = whole_job_rate(units_per_rank, world, e2e_s)
 
     kernel_id = plan.kernel
-    tile = plan.tile if kernel_id in (2, 3, 4) else None
+    tile = plan.tile if kernel_id in (2, 3, 4, 5) else None
     plan.close()
     del out, xin
     if rank != 0:

@@ -54,7 +54,7 @@ def lofar():
 def test_delay_table_and_kernel(lofar):
     assert lofar["plan"].maxshift == lofar["m"] == 20397
     assert np.array_equal(lofar["plan"].delays().astype(np.int64), lofar["d"])
-    assert lofar["plan"].kernel in (2, 3)       # autotuned: register-blocked or lane-interleaved
+    assert lofar["plan"].kernel in (2, 3, 5)    # autotuned: register-blocked, lane-interleaved or shared-subband
 
 
 def _check_sampled(x, d, nout, out, tile_samples, seed):
