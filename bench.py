@@ -36,13 +36,13 @@ METRIC = "DM-trial·samples/s"
 WORKLOAD = "lofar_f32"
 # ncu DRAM bytes (read + write) per de-dispersion launch, keyed by the
 # (tile configuration, raster group) the capture used
-PROFILED_TRAFFIC = {(5, 16): 25.63e9, (9, 16): 25.62e9}
+PROFILED_TRAFFIC = {(5, 16): 25.63e9, (11, 16): 21.41e9}
 
 # tile configurations of dd_plan_set_tile: (kernel, samples per thread or lane,
 # DM trials per thread or warp, warps per block)
 TILE_CONFIGS = {0: (2, 36, 4, 8), 1: (2, 20, 4, 12), 2: (2, 28, 4, 8), 3: (3, 16, 4, 8),
                 4: (3, 16, 8, 8), 5: (3, 16, 8, 4), 6: (3, 8, 16, 4), 7: (4, 20, 4, 8),
-                8: (4, 12, 8, 8), 9: (5, 16, 8, 4), 10: (5, 8, 8, 4)}
+                8: (4, 12, 8, 8), 9: (5, 16, 8, 4), 10: (5, 8, 8, 4), 11: (5, 16, 8, 6)}
 
 
 # ------------------------------------------------------------------ replicas (N > 1)
@@ -313,8 +313,9 @@ def run_ours(args, rank, world, local_rank):
             "achieved": achieved, "peak": peak, "unit": "Gadd/s", "frac": achieved / peak,
             "peak_basis": f"{sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",
             # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
-            # capture summarised in profiles/dedisp_kernel3_lofar_f32.md; only for
-            # the tile it was taken with (null otherwise)
+            # captures summarised in profiles/dedisp_kernel3_lofar_f32.md (config 5)
+            # and profiles/dedisp_kernel5_lofar_f32.md (config 11); only for the
+            # tile each was taken with (null otherwise)
             "traffic": PROFILED_TRAFFIC.get(tuple(tile[:2])) if tile else None,
             "traffic_unit": "bytes per launch",
             "kernel_ms": ker_ms}

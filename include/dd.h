@@ -182,8 +182,8 @@ DD_API int dd_process_host(dd_plan *plan, const void *in_host, int64_t in_pitch,
  * DM trial of the warp at a runtime column offset), 5 = shared subband
  * partial sums (the DM trials of a block whose delays relative to a 4-channel
  * subband's reference coincide share that subband's partial sum: the exact
- * brute-force result with fewer adds; needs at most 8 such delay patterns per
- * block and subband).  Kernels 2-5 share the tile-configuration list of
+ * brute-force result with fewer adds; needs at most 16 such delay patterns
+ * per block and subband).  Kernels 2-5 share the tile-configuration list of
  * dd_plan_set_tile.  Returns DD_ERR_ARG if the requested kernel cannot run
  * this plan. */
 DD_API int dd_plan_set_kernel(dd_plan *plan, int32_t kernel);
@@ -192,7 +192,7 @@ DD_API int dd_plan_set_kernel(dd_plan *plan, int32_t kernel);
 DD_API int dd_plan_get_kernel(const dd_plan *plan, int32_t *kernel);
 
 /* Autotuner for the tiled kernels: runs the plan on the caller's buffers
- * once per compiled tile configuration of kernels 2, 3 and 5 (0-6, 9, 10,
+ * once per compiled tile configuration of kernels 2, 3 and 5 (0-6, 9-11,
  * see dd_plan_set_tile) and raster group, times each with CUDA events on
  * `stream`, keeps the fastest for this plan and caches the choice
  * process-wide for plans of the same shape.  Kernel 4 is not timed (slower on
@@ -210,13 +210,13 @@ DD_API int dd_plan_autotune(dd_plan *plan, const void *in_dev, int64_t in_pitch,
  * 5: 16 x 8, 4 warps; 6: 8 x 16, 4 warps; kernel 4 (samples per lane x DM
  * trials per warp, warps) — 7: 20 x 4, 8 warps; 8: 12 x 8, 8 warps; kernel
  * 5 (samples per lane x DM trials per warp, warps; 4-channel subbands) — 9:
- * 16 x 8, 4 warps; 10: 8 x 8, 4 warps};
+ * 16 x 8, 4 warps; 10: 8 x 8, 4 warps; 11: 16 x 8, 6 warps};
  * raster_group (>= 1) is the number of DM blocks whose time tiles are swept
  * together.  DD_ERR_ARG if the configuration cannot run this plan. */
 DD_API int dd_plan_set_tile(dd_plan *plan, int32_t config, int32_t raster_group);
 
 /* Current tiled-kernel choice: configuration index, raster group, samples
- * per thread (kernel 2) or per lane (kernels 3, 4) and warps per block (any
+ * per thread (kernel 2) or per lane (kernels 3-5) and warps per block (any
  * pointer may be NULL).  DD_ERR_ARG if the tiled kernels cannot run this
  * plan. */
 DD_API int dd_plan_get_tile(const dd_plan *plan, int32_t *config, int32_t *raster_group,

@@ -297,9 +297,9 @@ int dd_plan_set_kernel(dd_plan *plan, int32_t kernel)
     }
     if (kernel == 3 || kernel == 4 || kernel == 5) {
         // the kernel's tile configurations, fastest measured first
-        static const int k3[] = {5, 3, 4, 6}, k4[] = {7, 8}, k5[] = {9, 10};
+        static const int k3[] = {5, 3, 4, 6}, k4[] = {7, 8}, k5[] = {11, 9, 10};
         const int *cfg = kernel == 3 ? k3 : kernel == 4 ? k4 : k5;
-        const int n = kernel == 3 ? 4 : 2;
+        const int n = kernel == 3 ? 4 : kernel == 4 ? 2 : 3;
         int rc = set_error(DD_ERR_ARG, "kernel %d is not available for this plan", kernel);
         for (int i = 0; plan->fast && i < n && rc != DD_OK; ++i) {
             rc = fast_set_tile(plan, cfg[i], 8);

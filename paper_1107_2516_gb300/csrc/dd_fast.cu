@@ -261,17 +261,19 @@ static void free_share(ShareCfgData &c)
 // of its t = t0 term.  c.ok stays false when the channel count is not a
 // multiple of kShCS, a (block, subband) has more than kShNP patterns, or the
 // buffers do not fit three blocks per SM.
-static int build_share(const dd_plan *p, int k, ShareCfgData &c)
+template <int DB>
+static int build_share_db(const dd_plan *p, int k, ShareCfgData &c)
 {
     c = ShareCfgData();
-    constexpr int CS = kShCS, DB = kShDR * kShNW, NP = kShNP;
+    constexpr int CS = kShCS, NP = kShNP;
     const int TILE = 32 * kShareCfg[k].ti, minb = kShareCfg[k].minb;
-    using R = ShareRecC;
+    using R = ShareRecDB<DB>;
     const int C = p->nchans, D = p->ndm;
     if (C % CS) return DD_OK;
     const int S = C / CS, nblk = (D + DB - 1) / DB;
     const int AL = elem_align(p->dtype);
     std::vector<int32_t> rec((size_t)nblk * S * R::kLen, 0), base((size_t)nblk * C);
+    std::vector<int> npat((size_t)nblk * S);
     auto dl = [&](int dm, int ch) { return p->delays[(size_t)std::min(dm, D - 1) * C + ch]; };
     long long need = 0;
     int pmax = 0;
@@ -293,7 +295,7 @@ static int build_share(const dd_plan *p, int k, ShareCfgData &c)
             }
             if ((int)pats.size() > NP) return DD_OK;
             int32_t *t = &rec[((size_t)b * S + s) * R::kLen];
-            t[R::kNpat] = (int32_t)pats.size();
+            int rowoff[CS];
             for (int cc = 0; cc < CS; ++cc) {
                 int lo = INT_MAX, hi = 0;
                 for (int j = 0; j < DB; ++j) {
@@ -302,40 +304,46 @@ static int build_share(const dd_plan *p, int k, ShareCfgData &c)
                 }
                 const int b0 = lo - (lo % AL);
                 base[(size_t)b * C + s * CS + cc] = b0;
-                t[R::kRowoff + cc] = dmin - b0;
+                rowoff[cc] = dmin - b0;
                 need = std::max<long long>(need, (long long)(hi - b0) + TILE);
             }
+            // patterns end to end in P; b_c without the row stride (added once rs is known)
             int poff = 0;
-            std::vector<int> plo(pats.size());
+            std::vector<int> plo(pats.size()), pof(pats.size());
             for (int k = 0; k < (int)pats.size(); ++k) {
                 int lo = INT_MAX, hi = INT_MIN;
                 for (int j = 0; j < DB; ++j)
                     if (pid[j] == k) { lo = std::min(lo, dref[j] - dmin); hi = std::max(hi, dref[j] - dmin); }
                 const int W = hi - lo + TILE;
                 int32_t *pr = t + R::kPat + k * R::kPatLen;
-                pr[0] = poff; pr[1] = lo; pr[2] = W;
-                for (int cc = 0; cc < CS; ++cc) pr[3 + cc] = pats[k][cc];
+                pr[0] = poff + W;
+                for (int cc = 0; cc < CS; ++cc) pr[1 + cc] = rowoff[cc] + lo + pats[k][cc] - poff;
                 plo[k] = lo;
+                pof[k] = poff;
                 poff += W;
             }
-            poff = 0;
-            std::vector<int> pof(pats.size());
-            for (int k = 0; k < (int)pats.size(); ++k) { pof[k] = poff; poff += t[R::kPat + k * R::kPatLen + 2]; }
+            t[R::kE] = poff;
             pmax = std::max(pmax, poff);
+            npat[(size_t)b * S + s] = (int)pats.size();
             for (int j = 0; j < DB; ++j) t[R::kTrial + j] = pof[pid[j]] + (dref[j] - dmin - plo[pid[j]]);
         }
     const int rs = (int)((need + 15) / 16 * 16);
+    for (size_t r = 0; r < npat.size(); ++r)
+        for (int k = 0; k < npat[r]; ++k)
+            for (int cc = 0; cc < CS; ++cc) rec[r * R::kLen + R::kPat + k * R::kPatLen + 1 + cc] += cc * rs;
     const size_t eb = in_elem_bytes(p->dtype);
-    // the shape's target blocks per SM if the buffers fit, else fewer (>= 2)
-    const size_t rows_b = (size_t)kShStages * CS * rs * eb, rec_b = (size_t)kShStages * R::kLen * 4;
-    const size_t p_b = (size_t)2 * ((pmax + 3) / 4 * 4) * 4;
-    const size_t bar_off = (rows_b + rec_b + p_b + 15) / 16 * 16;
-    const size_t need_b = bar_off + kShStages * sizeof(uint64_t);
+    // shared memory: input stages | records | 2 partial-sum buffers | mbarriers;
+    // the shape's target blocks per SM if it fits, else fewer (>= 2)
+    const int nis = kShareCfg[k].ns;
+    const int pm4 = (pmax + 3) / 4 * 4;
+    const size_t rows_b = (size_t)nis * CS * rs * eb, rec_b = (size_t)nis * R::kLen * 4;
+    const size_t bar_off = (rows_b + rec_b + (size_t)2 * pm4 * 4 + 15) / 16 * 16;
+    const size_t need_b = bar_off + nis * sizeof(uint64_t);
     bool fits = false;
-    for (int nb = minb; nb >= 2 && !fits; --nb)
+    for (int nb = minb; nb >= std::min(minb, 2) && !fits; --nb)
         fits = need_b <= std::min<size_t>(p->smem_optin, (228 * 1024) / nb - 1024) - 1024;
     if (!fits) return DD_OK;
-    c.nblk = nblk; c.nsub = S; c.rs = rs; c.pmax = (pmax + 3) / 4 * 4; c.bar_off = (int)bar_off;
+    c.nblk = nblk; c.nsub = S; c.rs = rs; c.pmax = pm4; c.bar_off = (int)bar_off;
     c.smem = need_b;
     cudaError_t e = cudaMalloc(&c.d_rec, rec.size() * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_base, base.size() * 4);
@@ -344,6 +352,15 @@ static int build_share(const dd_plan *p, int k, ShareCfgData &c)
     if (e != cudaSuccess) { free_share(c); return cuda_fail(e, "kernel 5 tables"); }
     c.ok = true;
     return DD_OK;
+}
+
+static int build_share(const dd_plan *p, int k, ShareCfgData &c)
+{
+    switch (kShareCfg[k].dr * kShareCfg[k].nw) {
+    case 32: return build_share_db<32>(p, k, c);
+    case 48: return build_share_db<48>(p, k, c);
+    default: c = ShareCfgData(); return DD_OK;
+    }
 }
 
 static void free_cfg(FastCfgData &c)
@@ -642,9 +659,15 @@ int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStre
     int bk = f->active, bg = f->dgroup, rc = DD_OK;
     // largest raster group first: on a tie (within 0.5%) it keeps the least DRAM traffic
     const int groups[] = {16, 8, 4};
-    // kernels 2, 3 and 5; kernel 4 (slower on every plan measured) runs only on request
-    for (int k = 0; k < kNumAllCfg && rc == DD_OK; ++k) {
-        if ((k >= kLaneEnd && k < kShareBeg) || !cfg_ok(f, k)) continue;
+    // kernels 5, 3 and 2, each in its order of measured speed, so that a tie
+    // keeps the earlier one (kernel 5's 48-trial shape first: fewest input
+    // re-reads); kernel 4 (slower on every plan measured) runs only on request
+    static const int order[] = {kShareBeg + 2, kShareBeg + 0, kShareBeg + 1, kNumFastCfg + 2, kNumFastCfg + 0,
+                                kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
+    static_assert(sizeof(order) / sizeof(order[0]) == kNumAllCfg - kNumTmemCfg, "every timed configuration once");
+    for (int k : order) {
+        if (rc != DD_OK) break;
+        if (!cfg_ok(f, k)) continue;
         rc = fast_run(p, k, 8, in, pitch, out, s);             // warm-up (caches, clocks)
         for (int gi = 0; gi < 3 && rc == DD_OK; ++gi) {
             cudaEventRecord(e0, s);
@@ -699,7 +722,7 @@ int fast_get_tile(const dd_plan *p, int *cfg, int *dgroup, int *tr, int *nw)
         if (nw) *nw = f->tm[f->active - kLaneEnd].nw;
     } else {
         if (tr) *tr = kShareCfg[f->active - kShareBeg].ti;
-        if (nw) *nw = kShNW;
+        if (nw) *nw = kShareCfg[f->active - kShareBeg].nw;
     }
     return DD_OK;
 }

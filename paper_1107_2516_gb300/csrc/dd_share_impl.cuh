@@ -13,36 +13,40 @@
 // and DR*NW DM trials.  Per subband (one TMA stage: its CS input rows and
 // its table record):
 //   stage 1: the block forms every pattern's partial sum over the samples
-//            its trials need (P, double-buffered in shared memory);
+//            its trials need (P, double-buffered in shared memory).  The
+//            patterns' sums are laid end to end in one index space e < E and
+//            the block's threads stride through it together, so every thread
+//            gets the same number of sums whatever the patterns' lengths;
 //   stage 2: each warp adds, for its trials, P_pat[t + offset] (one
 //            conflict-free shared word per add, as kernel 3).
 // One __syncthreads per subband: stage 1 of subband s+1 writes the other P
 // buffer while stage 2 of s reads this one; each warp takes its trials'
 // offsets into registers during stage 1 (the stage's record may be reused by
 // the next TMA copy before stage 2 ends).  The input ring has two stages
-// (kShStages): one subband's work covers the next one's copy, and the shared
-// memory saved keeps three blocks per SM.
+// (NS) stages: NS - 1 subbands' copies are in flight while one is summed.
 #pragma once
 
 #include "dd_lane_impl.cuh"
 
 namespace dd {
 
-constexpr int kShStages = 2;     // input ring of kernel 5
 
 // Table record of one (DM block, subband), int32 (16-byte multiple):
-//   [0 .. DB) q_j (index into P of trial j's t = t0 term) | [DB] npat |
-//   [DB+1 .. DB+1+CS) rowoff_c (staged-row index of u = 0 for channel c) |
-//   per pattern p < NPMAX: {poff, lo, W, r_0 .. r_{CS-1}}.
+//   [0 .. DB) q_j (index into P of trial j's t = t0 term) | [DB] E (the
+//   subband's P length) | 3 unused |
+//   per pattern p < NPMAX, kPatLen words: {end_p, b_0 .. b_{CS-1}, unused},
+// end_p = the index in P just past pattern p's sums, and b_c such that the
+// term of channel c in P[e] (e in pattern p) is staged element b_c + e of the
+// stage's rows (b_c = c * rs + the row offset of the pattern's first sample
+// minus the pattern's start in P).
 template <int CS, int NPMAX, int DB>
 struct ShareRec {
     static_assert(DB % 4 == 0, "trial offsets are loaded 4 at a time");
     static constexpr int kTrial = 0;
-    static constexpr int kNpat = DB;
-    static constexpr int kRowoff = DB + 1;
-    static constexpr int kPat = DB + 1 + CS;            // first pattern field
-    static constexpr int kPatLen = 3 + CS;
-    static constexpr int kLen = (kPat + NPMAX * kPatLen + 3) / 4 * 4;
+    static constexpr int kE = DB;
+    static constexpr int kPat = DB + 4;                 // first pattern field (16-byte aligned)
+    static constexpr int kPatLen = (1 + CS + 3) / 4 * 4;
+    static constexpr int kLen = kPat + NPMAX * kPatLen;
 };
 
 struct ShareLaunch {
@@ -60,7 +64,101 @@ struct ShareLaunch {
     size_t smem;
 };
 
-template <typename Tin, bool kInt, int TI, int DR, int NW, int CS, int NPMAX, int MINB>
+// Stage 1 of one subband: P[e] for e < E (the patterns' sums end to end),
+// threads t, t + nt, t + 2 nt, ...  Patterns are at least nt long, so a
+// thread moves on by at most one pattern per step.
+template <typename Tin, typename R, int CS>
+__device__ __forceinline__ void share_stage1(const int32_t *rec, const Tin *srow, float *Pb, int t, int nt)
+{
+    const int E = rec[R::kE];
+    const int32_t *pr = rec + R::kPat;
+    int f[R::kPatLen];
+#pragma unroll
+    for (int v = 0; v < R::kPatLen; v += 4) {
+        const int4 x = *reinterpret_cast<const int4 *>(pr + v);
+        f[v] = x.x; f[v + 1] = x.y; f[v + 2] = x.z; f[v + 3] = x.w;
+    }
+#pragma unroll 2
+    for (int e = t; e < E; e += nt) {
+        while (e >= f[0]) {
+            pr += R::kPatLen;
+#pragma unroll
+            for (int v = 0; v < R::kPatLen; v += 4) {
+                const int4 x = *reinterpret_cast<const int4 *>(pr + v);
+                f[v] = x.x; f[v + 1] = x.y; f[v + 2] = x.z; f[v + 3] = x.w;
+            }
+        }
+        float v = lane_ld<Tin>(srow + f[1] + e);
+#pragma unroll
+        for (int c = 1; c < CS; ++c) v += lane_ld<Tin>(srow + f[1 + c] + e);
+        Pb[e] = v;
+    }
+}
+
+// One thread's share of the block's partial statistics.
+template <bool kInt> struct ShareStat;
+template <> struct ShareStat<true> { long long n = 0, s = 0; unsigned long long q = 0; };
+template <> struct ShareStat<false> { int n = 0; float s = 0.f, q = 0.f; };
+
+// Store one warp's DR trials x 32*TI samples and accumulate their statistics.
+template <bool kInt, int TI, int DR>
+__device__ __forceinline__ void share_store(const ShareLaunch &a, const float (&acc)[DR][TI], int dmw, int64_t t0,
+                                            int lane, ShareStat<kInt> &st)
+{
+    const int64_t nout = a.nout;
+    if constexpr (kInt) {
+        int32_t *out = reinterpret_cast<int32_t *>(a.out);
+#pragma unroll
+        for (int j = 0; j < DR; ++j) {
+            const int dm = dmw + j;
+#pragma unroll
+            for (int i = 0; i < TI; ++i) {
+                const int64_t t = t0 + lane + 32 * i;
+                if (dm < a.ndm && t < nout) {
+                    const long long v = __float2int_rn(acc[j][i]);
+                    out[(size_t)dm * nout + t] = (int32_t)v;
+                    st.n++; st.s += v; st.q += (unsigned long long)(v * v);
+                }
+            }
+        }
+    } else {
+        float *out = reinterpret_cast<float *>(a.out);
+#pragma unroll
+        for (int j = 0; j < DR; ++j) {
+            const int dm = dmw + j;
+#pragma unroll
+            for (int i = 0; i < TI; ++i) {
+                const int64_t t = t0 + lane + 32 * i;
+                if (dm < a.ndm && t < nout) {
+                    out[(size_t)dm * nout + t] = acc[j][i];
+                    st.n++; st.s += acc[j][i];
+                }
+            }
+        }
+        const float m = st.n ? st.s / (float)st.n : 0.f;
+#pragma unroll
+        for (int j = 0; j < DR; ++j) {
+            const int dm = dmw + j;
+#pragma unroll
+            for (int i = 0; i < TI; ++i) {
+                const int64_t t = t0 + lane + 32 * i;
+                if (dm < a.ndm && t < nout) { const float d = acc[j][i] - m; st.q += d * d; }
+            }
+        }
+    }
+}
+
+// The block's partial statistics (every thread of the block calls this).
+template <bool kInt>
+__device__ __forceinline__ void share_stat_flush(const ShareLaunch &a, const ShareStat<kInt> &st)
+{
+    if constexpr (kInt)
+        block_stat_i(st.n, st.s, st.q, reinterpret_cast<StatI *>(a.partials) + blockIdx.x);
+    else
+        block_stat_f32(st.n, st.s, st.q, reinterpret_cast<StatF *>(a.partials) + blockIdx.x);
+}
+
+template <typename Tin, bool kInt, int TI, int DR, int NW, int CS, int NPMAX, int NS, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
 {
     constexpr int kDmBlk = DR * NW, kT = NW * 32;
@@ -79,42 +177,51 @@ __global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
     }
     const int dm0 = blk * kDmBlk;
 
-    // layout: [kShStages][CS][rs] Tin rows | [kShStages][kLen] int32 records |
+    // layout: [NS][CS][rs] Tin rows | [NS][kLen] int32 records |
     //         [2][pmax] float P | mbarriers
     const size_t stage_elems = (size_t)CS * rs;
     Tin *rows = reinterpret_cast<Tin *>(smem);
-    int32_t *srec = reinterpret_cast<int32_t *>(smem + kShStages * stage_elems * sizeof(Tin));
-    float *P = reinterpret_cast<float *>(srec + kShStages * R::kLen);
+    int32_t *srec = reinterpret_cast<int32_t *>(smem + NS * stage_elems * sizeof(Tin));
+    float *P = reinterpret_cast<float *>(srec + NS * R::kLen);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.bar_off);
     const int32_t *brec = a.rec + (size_t)blk * nsub * R::kLen;
     const int32_t *bbase = a.base + (size_t)blk * a.nchans;
 
     if (tid == 0) {
-        for (int s = 0; s < kShStages; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
         mbar_fence_init();
     }
     __syncthreads();
 
-    auto row_bytes = [&](int c, int64_t &g) -> uint32_t {
-        g = t0 + bbase[c];
+    // thread 0 issues subband s's copies with its rows' start offsets loaded
+    // one subband earlier (the global loads' latency stays off the barrier path)
+    auto row_bytes = [&](int b, int64_t &g) -> uint32_t {
+        g = t0 + b;
         int64_t n = a.nsamp_in_al - g;
         n = n < 0 ? 0 : (n > rs ? rs : n);
         return (uint32_t)(n * (int64_t)sizeof(Tin));
     };
-    auto issue = [&](int s) {
-        const int buf = s % kShStages;
+    auto issue = [&](int s, const int (&rb)[CS]) {
+        const int buf = s % NS;
         uint32_t bytes = (uint32_t)(R::kLen * sizeof(int32_t));
-        for (int cc = 0; cc < CS; ++cc) { int64_t g; bytes += row_bytes(s * CS + cc, g); }
+#pragma unroll
+        for (int cc = 0; cc < CS; ++cc) { int64_t g; bytes += row_bytes(rb[cc], g); }
         mbar_arrive_tx(&bar[buf], bytes);
         bulk_g2s(srec + (size_t)buf * R::kLen, brec + (size_t)s * R::kLen, (uint32_t)(R::kLen * sizeof(int32_t)),
                  &bar[buf]);
+#pragma unroll
         for (int cc = 0; cc < CS; ++cc) {
             int64_t g;
-            const uint32_t nb = row_bytes(s * CS + cc, g);
+            const uint32_t nb = row_bytes(rb[cc], g);
             if (nb)
                 bulk_g2s(rows + (size_t)buf * stage_elems + (size_t)cc * rs,
                          in + (size_t)(s * CS + cc) * a.pitch + g, nb, &bar[buf]);
         }
+    };
+    int rb[CS];
+    auto load_rb = [&](int s) {
+#pragma unroll
+        for (int cc = 0; cc < CS; ++cc) rb[cc] = bbase[s * CS + cc];
     };
 
     float acc[DR][TI];
@@ -123,37 +230,25 @@ __global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
 #pragma unroll
         for (int i = 0; i < TI; ++i) acc[j][i] = 0.f;
 
-    if (tid == 0)
-        for (int s = 0; s < kShStages - 1 && s < nsub; ++s) issue(s);
+    if (tid == 0) {
+        for (int s = 0; s < NS - 1 && s < nsub; ++s) { load_rb(s); issue(s, rb); }
+        if (NS - 1 < nsub) load_rb(NS - 1);
+    }
 
     bool ok = true;
     int q[DR];
     for (int s = 0; s < nsub; ++s) {
-        if (tid == 0 && s + kShStages - 1 < nsub) issue(s + kShStages - 1);
-        const int buf = s % kShStages;
-        if (ok) ok = mbar_wait(&bar[buf], (uint32_t)((s / kShStages) & 1), a.err);
+        if (tid == 0 && s + NS - 1 < nsub) {
+            issue(s + NS - 1, rb);
+            if (s + NS < nsub) load_rb(s + NS);
+        }
+        const int buf = s % NS;
+        if (ok) ok = mbar_wait(&bar[buf], (uint32_t)((s / NS) & 1), a.err);
         const int32_t *rec = srec + (size_t)buf * R::kLen;
         const Tin *srow = rows + (size_t)buf * stage_elems;
         float *Pb = P + (size_t)(s & 1) * a.pmax;
         // stage 1: every pattern's partial sum over the samples its trials need
-        const int npat = rec[R::kNpat];
-        int rowoff[CS];
-#pragma unroll
-        for (int c = 0; c < CS; ++c) rowoff[c] = rec[R::kRowoff + c];
-        for (int p = 0; p < npat; ++p) {
-            const int32_t *pr = rec + R::kPat + p * R::kPatLen;
-            const int poff = pr[0], lo = pr[1], W = pr[2];
-            const Tin *src[CS];
-#pragma unroll
-            for (int c = 0; c < CS; ++c) src[c] = srow + (size_t)c * rs + rowoff[c] + lo + pr[3 + c];
-#pragma unroll 4
-            for (int u = tid; u < W; u += kT) {
-                float v = lane_ld<Tin>(src[0] + u);
-#pragma unroll
-                for (int c = 1; c < CS; ++c) v += lane_ld<Tin>(src[c] + u);
-                Pb[poff + u] = v;
-            }
-        }
+        share_stage1<Tin, R, CS>(rec, srow, Pb, tid, kT);
         // this warp's trials: index of their t = t0 term in P
 #pragma unroll
         for (int j = 0; j < DR; j += 4) {
@@ -171,65 +266,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
     }
     ok = __syncthreads_and(ok);
     if (!ok) return;
-
-    const int64_t nout = a.nout;
-    if constexpr (kInt) {
-        long long n = 0, s = 0;
-        unsigned long long qq = 0;
-        int32_t *out = reinterpret_cast<int32_t *>(a.out);
-#pragma unroll
-        for (int j = 0; j < DR; ++j) {
-            const int dm = dm0 + warp * DR + j;
-#pragma unroll
-            for (int i = 0; i < TI; ++i) {
-                const int64_t t = t0 + lane + 32 * i;
-                if (dm < a.ndm && t < nout) {
-                    const long long v = __float2int_rn(acc[j][i]);
-                    out[(size_t)dm * nout + t] = (int32_t)v;
-                    n++; s += v; qq += (unsigned long long)(v * v);
-                }
-            }
-        }
-        block_stat_i(n, s, qq, reinterpret_cast<StatI *>(a.partials) + blockIdx.x);
-    } else {
-        int n = 0;
-        float s = 0.f;
-        float *out = reinterpret_cast<float *>(a.out);
-#pragma unroll
-        for (int j = 0; j < DR; ++j) {
-            const int dm = dm0 + warp * DR + j;
-#pragma unroll
-            for (int i = 0; i < TI; ++i) {
-                const int64_t t = t0 + lane + 32 * i;
-                if (dm < a.ndm && t < nout) {
-                    out[(size_t)dm * nout + t] = acc[j][i];
-                    n++; s += acc[j][i];
-                }
-            }
-        }
-        const float m = n ? s / (float)n : 0.f;
-        float qq = 0.f;
-#pragma unroll
-        for (int j = 0; j < DR; ++j) {
-            const int dm = dm0 + warp * DR + j;
-#pragma unroll
-            for (int i = 0; i < TI; ++i) {
-                const int64_t t = t0 + lane + 32 * i;
-                if (dm < a.ndm && t < nout) { const float d = acc[j][i] - m; qq += d * d; }
-            }
-        }
-        block_stat_f32(n, s, qq, reinterpret_cast<StatF *>(a.partials) + blockIdx.x);
-    }
+    ShareStat<kInt> st;
+    share_store<kInt, TI, DR>(a, acc, dm0 + warp * DR, t0, lane, st);
+    share_stat_flush<kInt>(a, st);
 }
 
-// Compiled shapes: subbands of 4 channels, at most 8 patterns per (block,
-// subband), 8 trials per warp, 4 warps (32 trials); {samples per lane,
-// resident blocks per SM the register budget targets}.
-constexpr int kShDR = 8, kShNW = 4, kShCS = 4, kShNP = 8;
-using ShareRecC = ShareRec<kShCS, kShNP, kShDR * kShNW>;
-struct ShareShape { int ti, minb; };
-constexpr int kNumShareCfg = 2;
-constexpr ShareShape kShareCfg[kNumShareCfg] = {{16, 3}, {8, 5}};
+// Compiled shapes: subbands of 4 channels, at most 16 patterns per (block,
+// subband); {samples per lane, DM trials per warp, warps, resident blocks per
+// SM the register budget targets, input stages}.
+constexpr int kShCS = 4, kShNP = 16;
+struct ShareShape { int ti, dr, nw, minb, ns; };
+constexpr int kNumShareCfg = 3;
+constexpr ShareShape kShareCfg[kNumShareCfg] = {{16, 8, 4, 3, 2}, {8, 8, 4, 5, 2}, {16, 8, 6, 2, 2}};
+template <int DB>
+using ShareRecDB = ShareRec<kShCS, kShNP, DB>;
 
 cudaError_t share_launch(int k, dd_dtype t, const ShareLaunch &a, cudaStream_t s);
 cudaError_t share_prepare(int k, size_t optin);

@@ -39,7 +39,7 @@ def main(argv=None):
     plan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, dms, wl.widths, wl.sigma, dd.DD_F32, a.nsamp)
     if a.kernel:
         plan.set_kernel(a.kernel)
-    if a.tile and plan.kernel in (2, 3, 4):
+    if a.tile and plan.kernel in (2, 3, 4, 5):
         plan.set_tile(*a.tile)
     g = torch.Generator(device="cuda")
     g.manual_seed(1)
@@ -57,7 +57,7 @@ def main(argv=None):
     if a.search:
         plan.search(out)
     units = len(dms) * plan.nsamp_out
-    tile = plan.tile if plan.kernel in (2, 3, 4) else None
+    tile = plan.tile if plan.kernel in (2, 3, 4, 5) else None
     print(f"kernel {plan.kernel} tile {tile} dms {a.dm_lo}+{len(dms)} nsamp {a.nsamp}: {ms:.2f} ms, "
           f"{units / (ms / 1e3):.3e} DM-trial.samples/s, {units * wl.nchans / ms / 1e9:.2f} Tadd/s")
     plan.close()

@@ -77,10 +77,10 @@ def test_sampled_points(lofar):
     _check_sampled(x, d, nout, out, 32 * lofar["plan"].tile[2], 123)
 
 
-@pytest.mark.parametrize("cfg", [7, 8, 9])
+@pytest.mark.parametrize("cfg", [7, 8, 9, 11])
 def test_kernel4_full_size(lofar, cfg):
     # the tensor-memory kernel (configs 7, 8) and the shared-subband kernel
-    # (config 9) on the full plan: sampled points and one whole row
+    # (configs 9, 11) on the full plan: sampled points and one whole row
     x, d, nout = lofar["x"], lofar["d"], lofar["nout"]
     wl = WL
     plan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, wl.sigma,

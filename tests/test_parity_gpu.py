@@ -104,7 +104,7 @@ def test_small_workload_parity(dtype, kernel):
 
 @pytest.mark.parametrize("tile", [(0, 1), (0, 3), (1, 8), (1, 2), (2, 16), (3, 8), (3, 1), (4, 4),
                                   (5, 8), (5, 3), (6, 16), (6, 2), (7, 8), (7, 3), (8, 16), (8, 1),
-                                  (9, 8), (9, 1)])
+                                  (9, 8), (9, 1), (10, 4), (11, 8), (11, 1)])
 @pytest.mark.parametrize("dtype", ["f32", "u8", "f16"])
 def test_small_workload_tile_configs(dtype, tile):
     # every compiled tile configuration of kernels 2-4 and several raster
@@ -116,9 +116,9 @@ def test_small_workload_tile_configs(dtype, tile):
                                               pulses=small_pulse(), kernel=2, tile=tile)
     except dd.DDError as e:
         # kernel 4 windows must fit the warp's TMEM buffer (config 8 does not
-        # at this plan's ~25 samples per DM step); kernel 5 needs at most 8
-        # delay patterns per block and 4-channel subband
-        assert tile[0] in (8, 9) and e.code == 1
+        # at this plan's ~25 samples per DM step); kernel 5 needs at most 16
+        # delay patterns per block and 4-channel subband (this plan has 29)
+        assert tile[0] in (8, 9, 10, 11) and e.code == 1
         pytest.skip("configuration unavailable for this plan")
     assert used == (2 if tile[0] < 3 else 3 if tile[0] < 7 else 4 if tile[0] < 9 else 5)
 
@@ -142,19 +142,36 @@ def test_kernel4_lofar_geometry(dtype, tile):
     assert used == 4
 
 
-@pytest.mark.parametrize("group", [8, 1])
+@pytest.mark.parametrize("tile", [(9, 8), (9, 1), (10, 16), (11, 8), (11, 1)])
 @pytest.mark.parametrize("dtype", ["f32", "u8", "f16"])
-def test_kernel5_lofar_full_band(dtype, group):
+def test_kernel5_lofar_full_band(dtype, tile):
     # the shared-subband kernel on the full LOFAR band (1024 channels: at most
-    # 7 delay patterns per 32-trial block and 4-channel subband), 100 trials
-    # (ragged last block), 2^15 samples, two pulses
+    # 8 delay patterns per block of 32 or 48 trials and 4-channel subband), 100
+    # trials (ragged last block), 2^15 samples, two pulses
     lw = synth.workload("lofar_f32")
     dms = [0.05 * i for i in range(100)]
     pulses = [synth.Pulse(dm=dms[61], t0=5000, width=8, amp=0.3),
               synth.Pulse(dm=dms[97], t0=9001, width=3, amp=0.5)]
     cands, out, ora, res, used = run_case(lw.nchans, lw.fch1, lw.foff, lw.tsamp, (1 << 15) + 17, dms,
                                           [1, 2, 4, 8, 16], 6.0, dtype, seed=78, pulses=pulses, kernel=5,
-                                          tile=(9, group), max_gray=2)
+                                          tile=tile, max_gray=2)
+    assert used == 5
+
+
+@pytest.mark.parametrize("tile", [(9, 8), (9, 1), (10, 1), (10, 16)])
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_kernel5_quarter_band(dtype, tile):
+    # 256 of the LOFAR band's channels (4x wider): up to 13 delay patterns per
+    # 32-trial block and subband, so many patterns per subband; ragged last
+    # block and sample tile
+    lw = synth.workload("lofar_f32")
+    nch, foff = 256, lw.foff * 4
+    dms = [0.05 * i for i in range(100)]
+    pulses = [synth.Pulse(dm=dms[61], t0=5000, width=8, amp=0.6),
+              synth.Pulse(dm=dms[97], t0=9001, width=3, amp=0.9)]
+    cands, out, ora, res, used = run_case(nch, lw.fch1, foff, lw.tsamp, (1 << 15) + 17, dms, [1, 2, 4, 8, 16],
+                                          6.0, dtype, seed=79, pulses=pulses, kernel=5, tile=tile,
+                                          max_gray=2)
     assert used == 5
 
 
@@ -167,7 +184,8 @@ def test_autotune_keeps_parity():
     out = torch.empty(wl.ndm * plan.nsamp_out, dtype=torch.float32, device="cuda")
     plan.autotune(x, wl.nsamp, out)
     cfg, group, tr, nw = plan.tile
-    assert cfg in (0, 1, 2, 3, 4, 5, 6, 9, 10) and group in (4, 8, 16) and tr in (8, 16, 20, 28, 36) and nw in (4, 8, 12)
+    assert cfg in (0, 1, 2, 3, 4, 5, 6, 9, 10, 11) and group in (4, 8, 16) and tr in (8, 16, 20, 28, 36) \
+        and nw in (4, 6, 8, 12)
     plan.execute(x, wl.nsamp, out)
     torch.cuda.synchronize()
     d_o, m_o = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
