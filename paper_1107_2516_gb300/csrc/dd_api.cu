@@ -440,9 +440,15 @@ int dd_process_host(dd_plan *plan, const void *in_host, int64_t in_pitch, dd_can
         plan->out_stage_bytes = out_bytes;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    e = cudaMemcpyAsync(plan->d_in_stage, in_host, in_bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail(e, "H2D input");
-    int rc = dd_execute(plan, plan->d_in_stage, in_pitch, plan->d_out_stage, stream);
+    // kernels 3 and 5: input copied in column chunks, each chunk's output tiles
+    // de-dispersed while the next chunk is in flight; otherwise copy, then execute
+    int rc = plan->kernel == 2 ? fast_execute_host(plan, in_host, in_pitch, plan->d_in_stage, plan->d_out_stage, s)
+                               : kNotPipelined;
+    if (rc == kNotPipelined) {
+        e = cudaMemcpyAsync(plan->d_in_stage, in_host, in_bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "H2D input");
+        rc = dd_execute(plan, plan->d_in_stage, in_pitch, plan->d_out_stage, stream);
+    }
     if (rc) return rc;
     return dd_search(plan, plan->d_out_stage, cand_host, capacity, n_found, stream);
 }

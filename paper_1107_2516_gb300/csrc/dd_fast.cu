@@ -34,6 +34,7 @@ struct LaneCfgData {
     bool ok = false;
     int ti = 0, dr = 0, nw = 0;
     int nblk = 0, rs = 0, ch = 0, bar_off = 0;
+    int64_t reach = 0;           // input columns a tile at t0 reads lie below t0 + reach
     size_t smem = 0;
     int32_t *d_offs = nullptr;   // [nblk][nchans][nw*dr] offsets within the staged row
     int32_t *d_base = nullptr;   // [nblk][nchans] row start relative to the tile start
@@ -51,6 +52,7 @@ struct TmemCfgData {
 struct ShareCfgData {
     bool ok = false;
     int nblk = 0, nsub = 0, rs = 0, pmax = 0, bar_off = 0;
+    int64_t reach = 0;           // input columns a tile at t0 reads lie below t0 + reach
     size_t smem = 0;
     int32_t *d_rec = nullptr;    // [nblk][nsub][kLen] subband records
     int32_t *d_base = nullptr;   // [nblk][nchans] staged row starts
@@ -63,6 +65,8 @@ constexpr int kLaneEnd = kNumFastCfg + kNumLaneCfg;
 constexpr int kShareBeg = kLaneEnd + kNumTmemCfg;
 constexpr int kNumAllCfg = kShareBeg + kNumShareCfg;
 
+constexpr int kHostChunks = 8;   // input column chunks of the pipelined host path
+
 struct FastPlan {
     FastCfgData cfg[kNumFastCfg];
     LaneCfgData lane[kNumLaneCfg];
@@ -72,6 +76,9 @@ struct FastPlan {
     int dgroup = 8;
     int al = 4;                  // row alignment in elements (16 bytes)
     int *d_err = nullptr;
+    // dd_process_host's pipelined input copy (created on first use)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev[kHostChunks + 1] = {};
 };
 
 static int elem_align(dd_dtype t) { return (int)(16 / in_elem_bytes(t)); }
@@ -155,6 +162,7 @@ static int build_lane(const dd_plan *p, int ti, int dr, int nw, int minb, LaneCf
     if (ch < 1) return DD_OK;
     c.bar_off = (int)(((size_t)kStages * ch * per_ch + 15) / 16 * 16);
     c.smem = (size_t)c.bar_off + kStages * sizeof(uint64_t);
+    c.reach = (int64_t)*std::max_element(base.begin(), base.end()) + rs;
     c.nblk = nblk; c.rs = rs; c.ch = ch;
     cudaError_t e = cudaMalloc(&c.d_offs, offs.size() * 4);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_base, base.size() * 4);
@@ -343,6 +351,7 @@ static int build_share_db(const dd_plan *p, int k, ShareCfgData &c)
     for (int nb = minb; nb >= std::min(minb, 2) && !fits; --nb)
         fits = need_b <= std::min<size_t>(p->smem_optin, (228 * 1024) / nb - 1024) - 1024;
     if (!fits) return DD_OK;
+    c.reach = (int64_t)*std::max_element(base.begin(), base.end()) + rs;
     c.nblk = nblk; c.nsub = S; c.rs = rs; c.pmax = pm4; c.bar_off = (int)bar_off;
     c.smem = need_b;
     cudaError_t e = cudaMalloc(&c.d_rec, rec.size() * 4);
@@ -535,24 +544,34 @@ int fast_error(dd_plan *p, cudaStream_t s)
     return DD_OK;
 }
 
-static int lane_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s)
+// Partial-statistics record size of the plan's input type.
+static size_t stat_bytes(const dd_plan *p) { return p->dtype == DD_U8 ? sizeof(StatI) : sizeof(StatF); }
+
+// Kernel 3 on output tiles [tile_lo, tile_hi) (tile_hi < 0: all tiles); the
+// partial statistics of tile j land where a whole-plan launch puts them.
+static int lane_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s,
+                    int64_t tile_lo = 0, int64_t tile_hi = -1)
 {
     FastPlan *f = static_cast<FastPlan *>(p->fast);
     LaneCfgData &c = f->lane[k];
     const int tile = 32 * c.ti;
     const int64_t ntile = (p->nsamp_out + tile - 1) / tile;
     if (ntile * c.nblk > INT32_MAX) return generic_execute(p, in, pitch, out, s);
+    if (tile_hi < 0) tile_hi = ntile;
     const int64_t np = ntile * c.nblk;
     int rc = ensure_partials_public(p, np);
     if (rc) return rc;
-    LaneLaunch a;
+    if (tile_hi <= tile_lo) return DD_OK;
+    LaneLaunch a{};
     a.in = in; a.pitch = pitch;
     a.nsamp_in_al = (p->nsamp_in + f->al - 1) / f->al * f->al;
     a.nchans = p->nchans; a.ndm = p->ndm; a.nout = p->nsamp_out;
     a.offs = c.d_offs; a.base = c.d_base;
     a.rs = c.rs; a.ch = c.ch; a.bar_off = c.bar_off; a.nblk = c.nblk;
-    a.ntile = ntile; a.dgroup = std::max(1, std::min(dgroup, c.nblk));
-    a.out = out; a.partials = p->d_partials; a.err = f->d_err; a.smem = c.smem;
+    a.ntile = tile_hi - tile_lo; a.t_base = tile_lo * tile;
+    a.dgroup = std::max(1, std::min(dgroup, c.nblk));
+    a.out = out; a.err = f->d_err; a.smem = c.smem;
+    a.partials = static_cast<char *>(p->d_partials) + (size_t)(tile_lo * c.nblk) * stat_bytes(p);
     cudaError_t e = launch_lane(k, p->dtype, a, s);
     if (e != cudaSuccess) return cuda_fail(e, "launch lane_kernel");
     p->n_partials = np;
@@ -585,24 +604,30 @@ static int tmem_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch
     return DD_OK;
 }
 
-static int share_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s)
+// Kernel 5 on output tiles [tile_lo, tile_hi), as lane_run.
+static int share_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitch, void *out, cudaStream_t s,
+                     int64_t tile_lo = 0, int64_t tile_hi = -1)
 {
     FastPlan *f = static_cast<FastPlan *>(p->fast);
     ShareCfgData &c = f->sh[k];
     const int tile = 32 * kShareCfg[k].ti;
     const int64_t ntile = (p->nsamp_out + tile - 1) / tile;
     if (ntile * c.nblk > INT32_MAX) return generic_execute(p, in, pitch, out, s);
+    if (tile_hi < 0) tile_hi = ntile;
     const int64_t np = ntile * c.nblk;
     int rc = ensure_partials_public(p, np);
     if (rc) return rc;
-    ShareLaunch a;
+    if (tile_hi <= tile_lo) return DD_OK;
+    ShareLaunch a{};
     a.in = in; a.pitch = pitch;
     a.nsamp_in_al = (p->nsamp_in + f->al - 1) / f->al * f->al;
     a.nchans = p->nchans; a.ndm = p->ndm; a.nsub = c.nsub; a.nout = p->nsamp_out;
     a.rec = c.d_rec; a.base = c.d_base;
     a.rs = c.rs; a.pmax = c.pmax; a.bar_off = c.bar_off; a.nblk = c.nblk;
-    a.ntile = ntile; a.dgroup = std::max(1, std::min(dgroup, c.nblk));
-    a.out = out; a.partials = p->d_partials; a.err = f->d_err; a.smem = c.smem;
+    a.ntile = tile_hi - tile_lo; a.t_base = tile_lo * tile;
+    a.dgroup = std::max(1, std::min(dgroup, c.nblk));
+    a.out = out; a.err = f->d_err; a.smem = c.smem;
+    a.partials = static_cast<char *>(p->d_partials) + (size_t)(tile_lo * c.nblk) * stat_bytes(p);
     cudaError_t e = share_launch(k, p->dtype, a, s);
     if (e != cudaSuccess) return cuda_fail(e, "launch share_kernel");
     p->n_partials = np;
@@ -645,6 +670,64 @@ int fast_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStrea
     // TMA bulk copies need 16-byte aligned rows; otherwise run the generic kernel.
     if (((uintptr_t)in & 15u) || (pitch % f->al)) return generic_execute(p, in, pitch, out, s);
     return fast_run(p, f->active, f->dgroup, in, pitch, out, s);
+}
+
+// dd_process_host with kernels 3 and 5: the input goes to the device in
+// kHostChunks column chunks on the plan's copy stream, and after chunk k the
+// output tiles whose input it completes run on `s` while the next chunk is
+// in flight.  Tile j (outputs from t0 = j * tile) reads input columns below
+// t0 + reach, so tiles [T_k, T_k+1) need columns below T_k+1 * tile + reach.
+// Returns kNotPipelined (nothing done) for the other kernels.
+int fast_execute_host(dd_plan *p, const void *in_host, int64_t pitch, void *in_dev, void *out, cudaStream_t s)
+{
+    FastPlan *f = static_cast<FastPlan *>(p->fast);
+    if (!f || ((uintptr_t)in_dev & 15u) || (pitch % f->al)) return kNotPipelined;
+    const int k = f->active;
+    int tile;
+    int64_t reach;
+    if (k >= kShareBeg) {
+        tile = 32 * kShareCfg[k - kShareBeg].ti;
+        reach = f->sh[k - kShareBeg].reach;
+    } else if (k >= kNumFastCfg && k < kLaneEnd) {
+        tile = 32 * f->lane[k - kNumFastCfg].ti;
+        reach = f->lane[k - kNumFastCfg].reach;
+    } else {
+        return kNotPipelined;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!f->copy_stream) {
+        e = cudaStreamCreateWithFlags(&f->copy_stream, cudaStreamNonBlocking);
+        for (int i = 0; i <= kHostChunks && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&f->copy_ev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "copy stream");
+    }
+    const size_t eb = in_elem_bytes(p->dtype);
+    const int64_t ntile = (p->nsamp_out + tile - 1) / tile;
+    const int nch = (int)std::min<int64_t>(kHostChunks, ntile);
+    // the copies wait for earlier work on `s` (it may still read the staging buffer)
+    e = cudaEventRecord(f->copy_ev[kHostChunks], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(f->copy_stream, f->copy_ev[kHostChunks], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "order input copy");
+    int64_t col = 0, tlo = 0;
+    for (int c = 0; c < nch; ++c) {
+        const int64_t thi = ntile * (c + 1) / nch;
+        int64_t end = c == nch - 1 ? pitch : std::min<int64_t>(pitch, (thi * tile + reach + 63) / 64 * 64);
+        if (end > col) {
+            e = cudaMemcpy2DAsync(static_cast<char *>(in_dev) + col * eb, (size_t)pitch * eb,
+                                  static_cast<const char *>(in_host) + col * eb, (size_t)pitch * eb,
+                                  (size_t)(end - col) * eb, (size_t)p->nchans, cudaMemcpyHostToDevice,
+                                  f->copy_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(f->copy_ev[c], f->copy_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, f->copy_ev[c], 0);
+            if (e != cudaSuccess) return cuda_fail(e, "H2D input chunk");
+            col = end;
+        }
+        const int rc = k >= kShareBeg ? share_run(p, k - kShareBeg, f->dgroup, in_dev, pitch, out, s, tlo, thi)
+                                      : lane_run(p, k - kNumFastCfg, f->dgroup, in_dev, pitch, out, s, tlo, thi);
+        if (rc) return rc;
+        tlo = thi;
+    }
+    return DD_OK;
 }
 
 int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStream_t s)
@@ -744,6 +827,12 @@ void fast_release(dd_plan *p)
     for (int k = 0; k < kNumTmemCfg; ++k) free_tmem(f->tm[k]);
     for (int k = 0; k < kNumShareCfg; ++k) free_share(f->sh[k]);
     if (f->d_err) cudaFree(f->d_err);
+    if (f->copy_stream) {
+        cudaStreamSynchronize(f->copy_stream);
+        for (int i = 0; i <= kHostChunks; ++i)
+            if (f->copy_ev[i]) cudaEventDestroy(f->copy_ev[i]);
+        cudaStreamDestroy(f->copy_stream);
+    }
     delete f;
     p->fast = nullptr;
 }

@@ -132,6 +132,11 @@ cudaError_t allow_max_dynamic_smem(const void *fn, size_t optin);
 // dd_fast.cu
 int fast_configure(dd_plan *p);
 int fast_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStream_t s);
+// dd_process_host's copy of in_host into in_dev pipelined with the
+// de-dispersion (kernels 3 and 5); kNotPipelined if the plan's kernel has no
+// such path (nothing is done then).
+constexpr int kNotPipelined = -1;
+int fast_execute_host(dd_plan *p, const void *in_host, int64_t pitch, void *in_dev, void *out, cudaStream_t s);
 void fast_release(dd_plan *p);
 int fast_error(dd_plan *p, cudaStream_t s);
 int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStream_t s);

@@ -30,6 +30,7 @@ struct LaneLaunch {
     int *err;
     size_t smem;
     int dtype;             // dd_dtype of `in` (batched launches)
+    int64_t t_base;        // lane_kernel: first output sample of the launch's tile range
 };
 
 template <typename Tin> __device__ __forceinline__ float lane_ld(const Tin *p);
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) lane_kernel(LaneLaunch a)
     int blk;
     int64_t t0;
     lane_raster<TI>(a, blockIdx.x, blk, t0);
+    t0 += a.t_base;
     uint32_t gstage = 0;
     lane_tile<Tin, kInt, TI, DR, NW>(a, blk, t0, blockIdx.x, smem, bar, gstage);
 }

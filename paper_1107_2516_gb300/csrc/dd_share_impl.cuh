@@ -57,7 +57,8 @@ struct ShareLaunch {
     const int32_t *rec;    // [nblk][nsub][kLen]
     const int32_t *base;   // [nblk][nchans] staged row start relative to the tile start (aligned)
     int rs, pmax, bar_off, nblk;
-    int64_t ntile;
+    int64_t ntile;         // tiles of this launch, starting at output sample t_base
+    int64_t t_base;
     int dgroup;
     void *out, *partials;
     int *err;
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
         LaneLaunch r{};
         r.dgroup = a.dgroup; r.ntile = a.ntile; r.nblk = a.nblk;
         lane_raster<TI>(r, blockIdx.x, blk, t0);
+        t0 += a.t_base;
     }
     const int dm0 = blk * kDmBlk;
 

@@ -294,3 +294,40 @@ def test_process_host_matches_device_path():
     c2, n2 = plan.search(out)
     assert n1 == n2 and keys(c1) == keys(c2)
     plan.close()
+
+
+@pytest.mark.parametrize("kernel,tile", [(3, (5, 8)), (3, (6, 1)), (5, (9, 4)), (5, (11, 16))])
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_process_host_pipelined(dtype, kernel, tile):
+    # dd_process_host with kernels 3 and 5 copies the input in 8 column chunks
+    # and de-disperses each chunk's output tiles as separate launches: same
+    # candidates and statistics as one device-resident execute + search (the
+    # partial statistics are combined in another order: FP32 path to 1e-12).
+    # Full LOFAR band, 100 trials, 2^15 + 17 samples, padded pitch, 4 sigma.
+    lw = synth.workload("lofar_f32")
+    dms = [0.05 * i for i in range(100)]
+    nsamp = (1 << 15) + 17
+    pitch = synth.aligned_pitch(nsamp + 40, 4 if dtype == "f32" else 1)
+    pulses = [synth.Pulse(dm=dms[61], t0=5000, width=8, amp=0.3),
+              synth.Pulse(dm=dms[97], t0=30001, width=3, amp=0.5)]
+    arr, _ = make_input(lw.nchans, nsamp, lw.fch1, lw.foff, lw.tsamp, 91, pulses, dtype, pitch)
+    plan = dd.Plan(lw.nchans, lw.fch1, lw.foff, lw.tsamp, dms, [1, 2, 4, 8, 16], 4.0, DTYPES[dtype], nsamp)
+    plan.set_kernel(kernel)
+    plan.set_tile(*tile)
+    host = torch.from_numpy(arr).pin_memory()
+    c1, n1 = plan.process_host(host, pitch, capacity=1 << 16)
+    mu1, sg1 = plan.stats()
+    out = torch.empty(len(dms) * plan.nsamp_out, dtype=torch.int32 if dtype == "u8" else torch.float32,
+                      device="cuda")
+    plan.execute(to_device(arr), pitch, out)
+    c2, n2 = plan.search(out, capacity=1 << 16)
+    mu2, sg2 = plan.stats()
+    assert plan.tile[0] == tile[0]
+    assert n1 == n2 and n1 > 100 and keys(c1) == keys(c2)
+    if dtype == "u8":
+        assert (mu1, sg1) == (mu2, sg2)
+        assert np.array_equal(c1["value"], c2["value"])
+    else:
+        assert abs(mu1 - mu2) <= 1e-12 * max(1.0, abs(mu2)) and abs(sg1 - sg2) <= 1e-12 * sg2
+        assert np.max(np.abs(c1["snr"].astype(np.float64) - c2["snr"])) <= 1e-4
+    plan.close()
