@@ -404,9 +404,11 @@ def run_batch(args):
     batch = dd.Batch(plans)
     batch.autotune(ins, pitches, outs, stream)
     batch.capture(ins, pitches, outs, stream)
-    # the sequential reference runs each plan with the batch's tile shape
-    for p in plans:
-        p.set_tile(batch.info[0], 8)
+    # the sequential reference runs each plan with the tile shape it has in the batch
+    beam_cfg = [batch.beam_config(i) for i in range(len(plans))]
+    for p, c in zip(plans, beam_cfg):
+        if c >= 0:
+            p.set_tile(c, 8)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
 
     def run_batch_once():
@@ -449,9 +451,10 @@ def run_batch(args):
         "config": {"workload": "24 uneven beams: 256-4096 ch, 2^16-2^20 samples, 500-4000 DMs, "
                    "fp32 + uint8, widths 1..32, 6 sigma", "units": units, "adds": adds,
                    "tile_config": cfg, "work_items": nitems, "separate_beams": nsep,
+                   "beams_on_kernel5": sum(1 for c in beam_cfg if c >= 9),
                    "launch": "persistent kernel + per-beam search, CUDA graph replay"},
         "sequential": {"value": units / (ms / 1e3), "ms_per_step": ms,
-                       "how": "each beam through dd_execute + dd_search in turn, same tile shape"},
+                       "how": "each beam through dd_execute + dd_search in turn, its batch tile shape"},
         "speedup_vs_sequential": ms / mb,
         "candidates": int(nb),
         "achieved_gadd_s": adds / (mb / 1e3) / 1e9, "alu_frac_of_peak": adds / (mb / 1e3) / 1e9 / peak,

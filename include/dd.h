@@ -270,14 +270,23 @@ DD_API int dd_batch_autotune(dd_batch *batch, const void *const *in_devs, const 
 
 /* Tile configuration the persistent launch uses (-1 if no beam uses it),
  * number of work items, and number of beams run by their own launch.  A new
- * batch starts with the first of configurations 5, 3, 6, 4, 1, 0, 2 (kernel
- * 3 shapes before kernel 2 shapes, see dd_plan_set_tile) that every tiled
- * beam can use. */
+ * batch starts with the first of configurations 9, 5, 3, 6, 4, 1, 0, 2 that
+ * every tiled beam can use.  Configuration 9 in a batch is mixed: kernel 5's
+ * 16 x 8, 4-warp shape for the beams whose kernel 5 tables exist and fit
+ * three blocks per SM, kernel 3's shape 5 (the same block geometry) for the
+ * others, in one persistent launch. */
 DD_API int dd_batch_info(const dd_batch *batch, int32_t *config, int64_t *nitems, int32_t *n_separate);
 
+/* Tile configuration beam `beam` runs in the persistent launch (9 or 5 under
+ * the mixed configuration 9, else the batch's), -1 if it runs by its own
+ * launch.  A plan set to that configuration alone (dd_plan_set_tile)
+ * reproduces the beam's batched output bit for bit. */
+DD_API int dd_batch_beam_config(const dd_batch *batch, int32_t beam, int32_t *config);
+
 /* Choose the persistent launch's tile configuration (0-6, dd_plan_set_tile's
- * kernel 2 and kernel 3 shapes); beams that cannot use it run by their own
- * launch.  Drops a captured graph.  DD_ERR_ARG for another index. */
+ * kernel 2 and kernel 3 shapes, or the mixed configuration 9); beams that
+ * cannot use it run by their own launch.  Drops a captured graph.  DD_ERR_ARG
+ * for another index. */
 DD_API int dd_batch_set_config(dd_batch *batch, int32_t config);
 
 /* ---------------------------------------------------------------------

@@ -852,6 +852,8 @@ struct dd_batch {
     int nitems = 0;
     dd::FastLaunch *d_beams = nullptr, *h_beams = nullptr;   // h_beams pinned (graph-capturable copy)
     dd::LaneLaunch *d_lbeams = nullptr, *h_lbeams = nullptr; // the same for kernel 3 configurations
+    dd::ShareLaunch *d_sbeams = nullptr, *h_sbeams = nullptr; // kernel 5 beams of the mixed configuration
+    std::vector<int> kind;                 // mixed configuration: 1 = the beam runs kernel 5
     unsigned int *d_counter = nullptr;
     int *d_err = nullptr;
     int bar_off = 0;
@@ -865,10 +867,24 @@ namespace dd {
 
 static FastPlan *fp(const dd_plan *p) { return static_cast<FastPlan *>(p->fast); }
 
-// Geometry of configuration k (kernel 2 or kernel 3) of a plan's tables.
+// The batch's mixed configuration: kernel 5 shape kMixedShare for the beams
+// whose tables exist and fit the shape's blocks per SM, kernel 3 shape
+// kMixedLane (the same block geometry) for the others.
+constexpr int kMixedCfg = kShareBeg + kMixedShare;
+
+static bool mixed_share_ok(const dd_plan *p, const FastPlan *f)
+{
+    const ShareCfgData &c = f->sh[kMixedShare];
+    const int nb = kShareCfg[kMixedShare].minb;
+    return c.ok && c.smem <= std::min<size_t>(p->smem_optin, (228 * 1024) / nb - 1024) - 1024;
+}
+
+// Geometry of configuration k (kernel 2 or kernel 3, or the mixed one: its
+// kernel 3 shape's) of a plan's tables.
 struct BatchGeom { bool ok; int tile, nblk, bar_off; };
 static BatchGeom batch_geom(const FastPlan *f, int k)
 {
+    if (k == kMixedCfg) k = kNumFastCfg + kMixedLane;
     if (!f || k < 0 || k >= kLaneEnd) return {false, 0, 0, 0};
     if (k < kNumFastCfg) {
         const FastCfgData &c = f->cfg[k];
@@ -904,6 +920,7 @@ static int batch_build(dd_batch *B, int k)
     });
     std::vector<uint2> items;
     int bar_off = 0;
+    B->kind.assign(B->plans.size(), 0);
     for (int i : order) {
         const dd_plan *p = B->plans[i];
         const BatchGeom c = batch_geom(fp(p), k);
@@ -912,13 +929,38 @@ static int batch_build(dd_batch *B, int k)
         if ((int64_t)items.size() + n > INT32_MAX) return set_error(DD_ERR_ARG, "batch too large");
         for (int64_t l = 0; l < n; ++l) items.push_back(make_uint2((unsigned)i, (unsigned)l));
         bar_off = std::max(bar_off, c.bar_off);
+        if (k == kMixedCfg && mixed_share_ok(p, fp(p))) {
+            B->kind[i] = 1;
+            bar_off = std::max(bar_off, fp(p)->sh[kMixedShare].bar_off);
+        }
+    }
+    if (k == kMixedCfg) {
+        // keep the shape's resident blocks per SM: the kernel 5 beams with the
+        // largest shared-memory layouts go back to kernel 3 until they fit
+        constexpr int nbar = kStages + kShareCfg[kMixedShare].ns;
+        int lane_off = 0;
+        for (int i : order) lane_off = std::max(lane_off, batch_geom(fp(B->plans[i]), k).bar_off);
+        for (;;) {
+            int worst = -1, off = lane_off;
+            for (int i : order)
+                if (B->kind[i]) {
+                    const int o = fp(B->plans[i])->sh[kMixedShare].bar_off;
+                    off = std::max(off, o);
+                    if (worst < 0 || o > fp(B->plans[worst])->sh[kMixedShare].bar_off) worst = i;
+                }
+            bar_off = off;
+            if (worst < 0 || off == lane_off ||
+                mixed_batch_occupancy((size_t)off + nbar * sizeof(uint64_t)) >= kShareCfg[kMixedShare].minb)
+                break;
+            B->kind[worst] = 0;
+        }
     }
     if (B->d_items) cudaFree(B->d_items);
     B->d_items = nullptr;
     B->nitems = (int)items.size();
     B->cfg = B->k2.empty() ? -1 : k;
     B->bar_off = bar_off;
-    B->smem = (size_t)bar_off + kStages * sizeof(uint64_t);
+    B->smem = (size_t)bar_off + (kStages + (k == kMixedCfg ? kShareCfg[kMixedShare].ns : 0)) * sizeof(uint64_t);
     if (!items.empty()) {
         cudaError_t e = cudaMalloc(&B->d_items, items.size() * sizeof(uint2));
         if (e == cudaSuccess)
@@ -952,7 +994,8 @@ static int batch_enqueue(dd_batch *B, const void *const *ins, const int64_t *pit
     if (rc) return rc;
     std::vector<int> own(B->sep);
     if (B->cfg >= kNumFastCfg) {
-        const int kl = B->cfg - kNumFastCfg;
+        const bool mixed = B->cfg == kMixedCfg;
+        const int kl = mixed ? kMixedLane : B->cfg - kNumFastCfg;
         for (int i : B->k2) {
             dd_plan *p = B->plans[i];
             FastPlan *f = fp(p);
@@ -969,16 +1012,33 @@ static int batch_enqueue(dd_batch *B, const void *const *ins, const int64_t *pit
             a.dgroup = std::max(1, std::min(f->dgroup, c.nblk));
             a.out = outs[i]; a.partials = p->d_partials; a.err = f->d_err; a.smem = B->smem;
             a.dtype = (int)p->dtype;
+            a.t_base = 0;
+            a.kind = mixed ? B->kind[i] : 0;
+            if (a.kind) {
+                const ShareCfgData &sc = f->sh[kMixedShare];
+                ShareLaunch &sa = B->h_sbeams[i];
+                sa = ShareLaunch{};
+                sa.in = ins[i]; sa.pitch = pitches[i];
+                sa.nsamp_in_al = a.nsamp_in_al;
+                sa.nchans = p->nchans; sa.ndm = p->ndm; sa.nsub = sc.nsub; sa.nout = p->nsamp_out;
+                sa.rec = sc.d_rec; sa.base = sc.d_base;
+                sa.rs = sc.rs; sa.pmax = sc.pmax; sa.bar_off = B->bar_off; sa.nblk = sc.nblk;
+                sa.ntile = a.ntile; sa.t_base = 0; sa.dgroup = a.dgroup;
+                sa.out = outs[i]; sa.partials = p->d_partials; sa.err = f->d_err; sa.smem = B->smem;
+            }
         }
         cudaError_t e = cudaMemcpyAsync(B->d_lbeams, B->h_lbeams, B->plans.size() * sizeof(LaneLaunch),
                                         cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && mixed)
+            e = cudaMemcpyAsync(B->d_sbeams, B->h_sbeams, B->plans.size() * sizeof(ShareLaunch),
+                                cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(B->d_counter, 0, sizeof(unsigned int), s);
         if (e != cudaSuccess) return cuda_fail(e, "batch setup");
         LaneBatchLaunch bl;
         bl.beams = B->d_lbeams; bl.items = B->d_items; bl.nitems = B->nitems;
-        bl.bar_off = B->bar_off; bl.counter = B->d_counter;
-        e = batch_launch_lane(kl, bl, B->grid, B->smem, s);
-        if (e != cudaSuccess) return cuda_fail(e, "launch lane_batch_kernel");
+        bl.bar_off = B->bar_off; bl.counter = B->d_counter; bl.sbeams = B->d_sbeams;
+        e = mixed ? mixed_batch_launch(bl, B->grid, B->smem, s) : batch_launch_lane(kl, bl, B->grid, B->smem, s);
+        if (e != cudaSuccess) return cuda_fail(e, mixed ? "launch mixed_batch_kernel" : "launch lane_batch_kernel");
         for (int i : B->k2) {
             dd_plan *p = B->plans[i];
             p->n_partials = B->h_lbeams[i].ntile * B->h_lbeams[i].nblk;
@@ -1055,7 +1115,7 @@ int dd_batch_create(dd_plan *const *plans, int32_t nplans, dd_batch **out)
     B->grid = std::max(1, plans[0]->sm_count);
     // first configuration, in the order of measured speed (kernel 3 shapes,
     // then kernel 2), that every tiled-kernel beam can use
-    static const int pref[] = {kNumFastCfg + 2, kNumFastCfg + 0, kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
+    static const int pref[] = {kMixedCfg, kNumFastCfg + 2, kNumFastCfg + 0, kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
     int k = -1;
     for (int c : pref) {
         if (k >= 0) break;
@@ -1073,6 +1133,9 @@ int dd_batch_create(dd_plan *const *plans, int32_t nplans, dd_batch **out)
     if (e == cudaSuccess) e = cudaMallocHost(&B->h_beams, nplans * sizeof(FastLaunch));
     if (e == cudaSuccess) e = cudaMalloc(&B->d_lbeams, nplans * sizeof(LaneLaunch));
     if (e == cudaSuccess) e = cudaMallocHost(&B->h_lbeams, nplans * sizeof(LaneLaunch));
+    if (e == cudaSuccess) e = cudaMalloc(&B->d_sbeams, nplans * sizeof(ShareLaunch));
+    if (e == cudaSuccess) e = cudaMallocHost(&B->h_sbeams, nplans * sizeof(ShareLaunch));
+    if (e == cudaSuccess) e = mixed_batch_prepare(plans[0]->smem_optin);
     if (e == cudaSuccess) e = cudaMalloc(&B->d_counter, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc(&B->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(B->d_err, 0, sizeof(int));
@@ -1080,6 +1143,7 @@ int dd_batch_create(dd_plan *const *plans, int32_t nplans, dd_batch **out)
     if (rc == DD_OK) {
         memset(B->h_beams, 0, nplans * sizeof(FastLaunch));
         memset(B->h_lbeams, 0, nplans * sizeof(LaneLaunch));
+        memset(B->h_sbeams, 0, nplans * sizeof(ShareLaunch));
         rc = batch_build(B, k);
     }
     if (rc != DD_OK) { dd_batch_destroy(B); return rc; }
@@ -1098,6 +1162,8 @@ int dd_batch_destroy(dd_batch *B)
     if (B->h_beams) cudaFreeHost(B->h_beams);
     if (B->d_lbeams) cudaFree(B->d_lbeams);
     if (B->h_lbeams) cudaFreeHost(B->h_lbeams);
+    if (B->d_sbeams) cudaFree(B->d_sbeams);
+    if (B->h_sbeams) cudaFreeHost(B->h_sbeams);
     if (B->d_counter) cudaFree(B->d_counter);
     if (B->d_err) cudaFree(B->d_err);
     delete B;
@@ -1165,7 +1231,11 @@ int dd_batch_autotune(dd_batch *B, const void *const *ins, const int64_t *pitche
         return set_error(DD_ERR_CUDA, "cudaEventCreate");
     float best = 1e30f;
     int bk = B->cfg, rc = DD_OK;
-    for (int k = 0; k < kLaneEnd && rc == DD_OK; ++k) {
+    std::vector<int> cfgs;
+    for (int k = 0; k < kLaneEnd; ++k) cfgs.push_back(k);
+    cfgs.push_back(kMixedCfg);
+    for (int k : cfgs) {
+        if (rc != DD_OK) break;
         bool all = true;
         for (int i = 0; i < (int)B->plans.size(); ++i) {
             const FastPlan *f = fp(B->plans[i]);
@@ -1191,11 +1261,23 @@ int dd_batch_autotune(dd_batch *B, const void *const *ins, const int64_t *pitche
 int dd_batch_set_config(dd_batch *B, int32_t config)
 {
     if (!B) return set_error(DD_ERR_ARG, "batch is NULL");
-    if (config < 0 || config >= kLaneEnd) return set_error(DD_ERR_ARG, "batch configuration %d out of range", config);
+    if ((config < 0 || config >= kLaneEnd) && config != kMixedCfg)
+        return set_error(DD_ERR_ARG, "batch configuration %d out of range", config);
     cudaDeviceSynchronize();
     if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
     if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
     return batch_build(B, config);
+}
+
+int dd_batch_beam_config(const dd_batch *B, int32_t beam, int32_t *config)
+{
+    if (!B || !config) return set_error(DD_ERR_ARG, "NULL argument");
+    if (beam < 0 || beam >= (int32_t)B->plans.size()) return set_error(DD_ERR_ARG, "beam %d out of range", beam);
+    *config = -1;
+    if (B->cfg < 0 || std::find(B->k2.begin(), B->k2.end(), beam) == B->k2.end()) return DD_OK;
+    if (B->cfg == kMixedCfg) *config = B->kind[beam] ? kMixedCfg : kNumFastCfg + kMixedLane;
+    else *config = B->cfg;
+    return DD_OK;
 }
 
 int dd_batch_info(const dd_batch *B, int32_t *config, int64_t *nitems, int32_t *n_separate)

@@ -31,6 +31,7 @@ struct LaneLaunch {
     size_t smem;
     int dtype;             // dd_dtype of `in` (batched launches)
     int64_t t_base;        // lane_kernel: first output sample of the launch's tile range
+    int kind;              // mixed batch: 0 = this kernel 3 launch, 1 = the beam's kernel 5 launch
 };
 
 template <typename Tin> __device__ __forceinline__ float lane_ld(const Tin *p);
@@ -56,10 +57,15 @@ __device__ __forceinline__ void lane_raster(const LaneLaunch &a, int64_t lin, in
 // mbarrier ring persists across the items of a persistent block: stage s
 // of this item uses buffer (gstage+s) % kStages, parity (gstage+s) / kStages).
 // Returns false if a bounded wait gave up.
+// The tile addresses the block's dynamic shared memory through the extern
+// symbol (not a pointer argument), so that its loads and stores stay
+// shared-space instructions in the out-of-line copies the persistent kernels
+// call.
 template <typename Tin, bool kInt, int TI, int DR, int NW>
 __device__ __forceinline__ bool lane_tile(const LaneLaunch &a, int blk, int64_t t0, int64_t lin,
-                                          unsigned char *smem, uint64_t *bar, uint32_t &gstage)
+                                          uint64_t *bar, uint32_t &gstage)
 {
+    extern __shared__ __align__(128) unsigned char smem[];
     constexpr int kDmBlk = DR * NW;
     const Tin *__restrict__ in = static_cast<const Tin *>(a.in);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -208,27 +214,30 @@ __global__ void __launch_bounds__(NW * 32, MINB) lane_kernel(LaneLaunch a)
     lane_raster<TI>(a, blockIdx.x, blk, t0);
     t0 += a.t_base;
     uint32_t gstage = 0;
-    lane_tile<Tin, kInt, TI, DR, NW>(a, blk, t0, blockIdx.x, smem, bar, gstage);
+    lane_tile<Tin, kInt, TI, DR, NW>(a, blk, t0, blockIdx.x, bar, gstage);
 }
 
 // lane_tile as an out-of-line function: the persistent kernel calls one per
 // input type, each compiled with the full register budget.
 template <typename Tin, bool kInt, int TI, int DR, int NW>
 __device__ __noinline__ bool lane_tile_call(const LaneLaunch &a, int blk, int64_t t0, int64_t lin,
-                                            unsigned char *smem, uint64_t *bar, uint32_t &gstage)
+                                            uint64_t *bar, uint32_t &gstage)
 {
-    return lane_tile<Tin, kInt, TI, DR, NW>(a, blk, t0, lin, smem, bar, gstage);
+    return lane_tile<Tin, kInt, TI, DR, NW>(a, blk, t0, lin, bar, gstage);
 }
 
 // Batched plans with kernel 3: a persistent grid (MINB blocks per SM) pulls
 // work items (beam, linear tile index) from a device queue, heaviest beams
 // first; each beam brings its own tables, buffers and input type.
+struct ShareLaunch;
+
 struct LaneBatchLaunch {
     const LaneLaunch *beams;
     const uint2 *items;
     int nitems;
     int bar_off;
     unsigned int *counter;
+    const ShareLaunch *sbeams;   // mixed batch: each kind-1 beam's kernel 5 launch
 };
 
 template <int TI, int DR, int NW, int MINB>
@@ -256,9 +265,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) lane_batch_kernel(LaneBatchLaun
         lane_raster<TI>(a, w.y, blk, t0);
         bool ok;
         switch (a.dtype) {
-        case DD_F32: ok = lane_tile_call<float, false, TI, DR, NW>(a, blk, t0, w.y, smem, bar, gstage); break;
-        case DD_F16: ok = lane_tile_call<__half, false, TI, DR, NW>(a, blk, t0, w.y, smem, bar, gstage); break;
-        default: ok = lane_tile_call<uint8_t, true, TI, DR, NW>(a, blk, t0, w.y, smem, bar, gstage); break;
+        case DD_F32: ok = lane_tile_call<float, false, TI, DR, NW>(a, blk, t0, w.y, bar, gstage); break;
+        case DD_F16: ok = lane_tile_call<__half, false, TI, DR, NW>(a, blk, t0, w.y, bar, gstage); break;
+        default: ok = lane_tile_call<uint8_t, true, TI, DR, NW>(a, blk, t0, w.y, bar, gstage); break;
         }
         if (!ok) break;
         __syncthreads();

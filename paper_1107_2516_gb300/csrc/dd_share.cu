@@ -47,4 +47,32 @@ cudaError_t share_prepare(int k, size_t optin)
     }
 }
 
+// Mixed persistent batch: kernel 5 shape 0 with kernel 3 shape 2.
+constexpr ShareShape kMS = kShareCfg[kMixedShare];
+constexpr LaneShape kML = kLaneCfg[kMixedLane];
+static_assert(kMS.ti == kML.ti && kMS.dr == kML.dr && kMS.nw == kML.nw && kMS.minb == kML.minb,
+              "the mixed batch's kernel 3 and kernel 5 shapes must share the block geometry");
+
+cudaError_t mixed_batch_launch(const LaneBatchLaunch &b, int sms, size_t smem, cudaStream_t s)
+{
+    mixed_batch_kernel<kMS.ti, kMS.dr, kMS.nw, kShCS, kShNP, kMS.ns, kMS.minb><<<sms * kMS.minb, kMS.nw * 32, smem, s>>>(b);
+    return cudaGetLastError();
+}
+
+int mixed_batch_occupancy(size_t smem)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &n, mixed_batch_kernel<kMS.ti, kMS.dr, kMS.nw, kShCS, kShNP, kMS.ns, kMS.minb>, kMS.nw * 32, smem) !=
+        cudaSuccess)
+        return 0;
+    return n;
+}
+
+cudaError_t mixed_batch_prepare(size_t optin)
+{
+    return allow_max_dynamic_smem((const void *)mixed_batch_kernel<kMS.ti, kMS.dr, kMS.nw, kShCS, kShNP, kMS.ns, kMS.minb>,
+                                  optin);
+}
+
 }  // namespace dd

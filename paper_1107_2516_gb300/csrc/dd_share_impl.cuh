@@ -149,51 +149,43 @@ __device__ __forceinline__ void share_store(const ShareLaunch &a, const float (&
     }
 }
 
-// The block's partial statistics (every thread of the block calls this).
+// The block's partial statistics into record `lin` (every thread of the
+// block calls this).
 template <bool kInt>
-__device__ __forceinline__ void share_stat_flush(const ShareLaunch &a, const ShareStat<kInt> &st)
+__device__ __forceinline__ void share_stat_flush(const ShareLaunch &a, const ShareStat<kInt> &st, int64_t lin)
 {
     if constexpr (kInt)
-        block_stat_i(st.n, st.s, st.q, reinterpret_cast<StatI *>(a.partials) + blockIdx.x);
+        block_stat_i(st.n, st.s, st.q, reinterpret_cast<StatI *>(a.partials) + lin);
     else
-        block_stat_f32(st.n, st.s, st.q, reinterpret_cast<StatF *>(a.partials) + blockIdx.x);
+        block_stat_f32(st.n, st.s, st.q, reinterpret_cast<StatF *>(a.partials) + lin);
 }
 
-template <typename Tin, bool kInt, int TI, int DR, int NW, int CS, int NPMAX, int NS, int MINB>
-__global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
+// One work item: DM block `blk` x the time tile at t0; partial statistics
+// record `lin`.  bar[NS] is the block's input ring; `gstage` its running stage
+// count (a persistent block keeps the ring across items: subband s of this
+// item uses buffer (gstage + s) % NS, parity ((gstage + s) / NS) & 1).
+// Returns false if a bounded wait gave up.
+template <typename Tin, bool kInt, int TI, int DR, int NW, int CS, int NPMAX, int NS>
+__device__ __forceinline__ bool share_tile(const ShareLaunch &a, int blk, int64_t t0, int64_t lin,
+                                           uint64_t *bar, uint32_t &gstage)
 {
+    extern __shared__ __align__(128) unsigned char smem[];   // as lane_tile: shared-space accesses
     constexpr int kDmBlk = DR * NW, kT = NW * 32;
     using R = ShareRec<CS, NPMAX, kDmBlk>;
-    extern __shared__ __align__(128) unsigned char smem[];
     const Tin *__restrict__ in = static_cast<const Tin *>(a.in);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int rs = a.rs, nsub = a.nsub;
-
-    int blk;
-    int64_t t0;
-    {
-        LaneLaunch r{};
-        r.dgroup = a.dgroup; r.ntile = a.ntile; r.nblk = a.nblk;
-        lane_raster<TI>(r, blockIdx.x, blk, t0);
-        t0 += a.t_base;
-    }
     const int dm0 = blk * kDmBlk;
 
-    // layout: [NS][CS][rs] Tin rows | [NS][kLen] int32 records |
-    //         [2][pmax] float P | mbarriers
+    // layout: [NS][CS][rs] Tin rows | [NS][kLen] int32 records | [2][pmax] float P
     const size_t stage_elems = (size_t)CS * rs;
     Tin *rows = reinterpret_cast<Tin *>(smem);
     int32_t *srec = reinterpret_cast<int32_t *>(smem + NS * stage_elems * sizeof(Tin));
     float *P = reinterpret_cast<float *>(srec + NS * R::kLen);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.bar_off);
     const int32_t *brec = a.rec + (size_t)blk * nsub * R::kLen;
     const int32_t *bbase = a.base + (size_t)blk * a.nchans;
-
-    if (tid == 0) {
-        for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
+    const uint32_t g0 = gstage;
+    gstage += (uint32_t)nsub;
 
     // thread 0 issues subband s's copies with its rows' start offsets loaded
     // one subband earlier (the global loads' latency stays off the barrier path)
@@ -204,7 +196,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
         return (uint32_t)(n * (int64_t)sizeof(Tin));
     };
     auto issue = [&](int s, const int (&rb)[CS]) {
-        const int buf = s % NS;
+        const int buf = (int)((g0 + s) % NS);
         uint32_t bytes = (uint32_t)(R::kLen * sizeof(int32_t));
 #pragma unroll
         for (int cc = 0; cc < CS; ++cc) { int64_t g; bytes += row_bytes(rb[cc], g); }
@@ -244,8 +236,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
             issue(s + NS - 1, rb);
             if (s + NS < nsub) load_rb(s + NS);
         }
-        const int buf = s % NS;
-        if (ok) ok = mbar_wait(&bar[buf], (uint32_t)((s / NS) & 1), a.err);
+        const int buf = (int)((g0 + s) % NS);
+        if (ok) ok = mbar_wait(&bar[buf], (uint32_t)(((g0 + s) / NS) & 1), a.err);
         const int32_t *rec = srec + (size_t)buf * R::kLen;
         const Tin *srow = rows + (size_t)buf * stage_elems;
         float *Pb = P + (size_t)(s & 1) * a.pmax;
@@ -267,10 +259,92 @@ __global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
         }
     }
     ok = __syncthreads_and(ok);
-    if (!ok) return;
+    if (!ok) return false;
     ShareStat<kInt> st;
     share_store<kInt, TI, DR>(a, acc, dm0 + warp * DR, t0, lane, st);
-    share_stat_flush<kInt>(a, st);
+    share_stat_flush<kInt>(a, st, lin);
+    return true;
+}
+
+// One plan: one block per work item, grid = nblk * ntile.
+template <typename Tin, bool kInt, int TI, int DR, int NW, int CS, int NPMAX, int NS, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + a.bar_off);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int blk;
+    int64_t t0;
+    {
+        LaneLaunch r{};
+        r.dgroup = a.dgroup; r.ntile = a.ntile; r.nblk = a.nblk;
+        lane_raster<TI>(r, blockIdx.x, blk, t0);
+        t0 += a.t_base;
+    }
+    uint32_t gstage = 0;
+    share_tile<Tin, kInt, TI, DR, NW, CS, NPMAX, NS>(a, blk, t0, blockIdx.x, bar, gstage);
+}
+
+// share_tile as an out-of-line function for the persistent batch kernel.
+template <typename Tin, bool kInt, int TI, int DR, int NW, int CS, int NPMAX, int NS>
+__device__ __noinline__ bool share_tile_call(const ShareLaunch &a, int blk, int64_t t0, int64_t lin,
+                                             uint64_t *bar, uint32_t &gstage)
+{
+    return share_tile<Tin, kInt, TI, DR, NW, CS, NPMAX, NS>(a, blk, t0, lin, bar, gstage);
+}
+
+// Persistent batch of beams, each on kernel 5 (kind 1: its ShareLaunch) or on
+// kernel 3 (kind 0: its LaneLaunch) with the same block geometry (DR*NW
+// trials x 32*TI samples), so both enumerate the same work items.  Two input
+// rings: kernel 3's kStages mbarriers at b.bar_off, kernel 5's NS right after;
+// each with its own running stage count.
+template <int TI, int DR, int NW, int CS, int NPMAX, int NS, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) mixed_batch_kernel(LaneBatchLaunch b)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_item;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + b.bar_off), *sbar = bar + kStages;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < NS; ++s) mbar_init(&sbar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t gl = 0, gs = 0;
+    while (true) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(b.counter, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= b.nitems) break;
+        const uint2 w = b.items[it];
+        const LaneLaunch &a = b.beams[w.x];
+        int blk;
+        int64_t t0;
+        lane_raster<TI>(a, w.y, blk, t0);
+        bool ok;
+        if (a.kind == 1) {
+            const ShareLaunch &sa = b.sbeams[w.x];
+            switch (a.dtype) {
+            case DD_F32: ok = share_tile_call<float, false, TI, DR, NW, CS, NPMAX, NS>(sa, blk, t0, w.y, sbar, gs); break;
+            case DD_F16: ok = share_tile_call<__half, false, TI, DR, NW, CS, NPMAX, NS>(sa, blk, t0, w.y, sbar, gs); break;
+            default: ok = share_tile_call<uint8_t, true, TI, DR, NW, CS, NPMAX, NS>(sa, blk, t0, w.y, sbar, gs); break;
+            }
+        } else {
+            switch (a.dtype) {
+            case DD_F32: ok = lane_tile_call<float, false, TI, DR, NW>(a, blk, t0, w.y, bar, gl); break;
+            case DD_F16: ok = lane_tile_call<__half, false, TI, DR, NW>(a, blk, t0, w.y, bar, gl); break;
+            default: ok = lane_tile_call<uint8_t, true, TI, DR, NW>(a, blk, t0, w.y, bar, gl); break;
+            }
+        }
+        if (!ok) break;
+        __syncthreads();
+        if (threadIdx.x == 0) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
 }
 
 // Compiled shapes: subbands of 4 channels, at most 16 patterns per (block,
@@ -285,5 +359,11 @@ using ShareRecDB = ShareRec<kShCS, kShNP, DB>;
 
 cudaError_t share_launch(int k, dd_dtype t, const ShareLaunch &a, cudaStream_t s);
 cudaError_t share_prepare(int k, size_t optin);
+// Mixed persistent batch of kernel 5 shape 0 and kernel 3 shape 2 (the same
+// block geometry): grid = sms * that shape's resident blocks per SM.
+cudaError_t mixed_batch_launch(const LaneBatchLaunch &b, int sms, size_t smem, cudaStream_t s);
+cudaError_t mixed_batch_prepare(size_t optin);
+int mixed_batch_occupancy(size_t smem);   // resident blocks per SM with `smem` dynamic bytes
+constexpr int kMixedLane = 2, kMixedShare = 0;
 
 }  // namespace dd

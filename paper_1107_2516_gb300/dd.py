@@ -30,7 +30,7 @@ EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "d
            "dd_plan_autotune", "dd_plan_set_tile", "dd_plan_get_tile",
            "dd_stats_f32_noalloc", "dd_last_error", "dd_version",
            "dd_batch_create", "dd_batch_destroy", "dd_batch_execute", "dd_batch_capture",
-           "dd_batch_launch", "dd_batch_results", "dd_batch_autotune", "dd_batch_info", "dd_batch_set_config",
+           "dd_batch_launch", "dd_batch_results", "dd_batch_autotune", "dd_batch_info", "dd_batch_set_config", "dd_batch_beam_config",
            "dd_server_create", "dd_server_destroy", "dd_server_add_beam", "dd_server_remove_beam",
            "dd_server_submit", "dd_server_poll", "dd_server_candidates", "dd_server_beam_info",
            "dd_server_memory", "dd_subband_plan_create", "dd_subband_plan_destroy",
@@ -100,6 +100,7 @@ def load(path: Optional[str] = None):
             "dd_batch_autotune": (C.c_int, [vp, vp, vp, vp, vp]),
             "dd_batch_info": (C.c_int, [vp, C.POINTER(i32), P64, C.POINTER(i32)]),
             "dd_batch_set_config": (C.c_int, [vp, i32]),
+            "dd_batch_beam_config": (C.c_int, [vp, i32, C.POINTER(i32)]),
             "dd_server_create": (C.c_int, [i64, i32, i64, C.POINTER(vp)]),
             "dd_server_destroy": (C.c_int, [vp]),
             "dd_server_add_beam": (C.c_int, [vp, i32, f64, f64, f64, vp, i32, vp, i32, f64, i32, i64,
@@ -331,6 +332,12 @@ def dd_batch_set_config(batch: int, config: int) -> None:
     _check(load().dd_batch_set_config(batch, int(config)))
 
 
+def dd_batch_beam_config(batch: int, beam: int) -> int:
+    c = C.c_int32()
+    _check(load().dd_batch_beam_config(batch, int(beam), C.byref(c)))
+    return int(c.value)
+
+
 class Server:
     """Owning wrapper around a dd_server handle (marshalling only)."""
 
@@ -436,6 +443,10 @@ class Batch:
 
     def set_config(self, config):
         dd_batch_set_config(self.handle, config)
+
+    def beam_config(self, beam):
+        """Tile configuration beam `beam` runs in the persistent launch (-1: its own launch)."""
+        return dd_batch_beam_config(self.handle, beam)
 
     def close(self):
         if self.handle:
