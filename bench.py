@@ -452,7 +452,8 @@ def run_batch(args):
                    "fp32 + uint8, widths 1..32, 6 sigma", "units": units, "adds": adds,
                    "tile_config": cfg, "work_items": nitems, "separate_beams": nsep,
                    "beams_on_kernel5": sum(1 for c in beam_cfg if c >= 9),
-                   "launch": "persistent kernel + per-beam search, CUDA graph replay"},
+                   "launch": ("each beam's own de-dispersion launch" if batch.per_beam else "persistent kernel")
+                             + " + per-beam search, CUDA graph replay (the batch autotuner's choice)"},
         "sequential": {"value": units / (ms / 1e3), "ms_per_step": ms,
                        "how": "each beam through dd_execute + dd_search in turn, its batch tile shape"},
         "speedup_vs_sequential": ms / mb,

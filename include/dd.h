@@ -277,10 +277,21 @@ DD_API int dd_batch_autotune(dd_batch *batch, const void *const *in_devs, const 
  * others, in one persistent launch. */
 DD_API int dd_batch_info(const dd_batch *batch, int32_t *config, int64_t *nitems, int32_t *n_separate);
 
-/* Tile configuration beam `beam` runs in the persistent launch (9 or 5 under
- * the mixed configuration 9, else the batch's), -1 if it runs by its own
- * launch.  A plan set to that configuration alone (dd_plan_set_tile)
- * reproduces the beam's batched output bit for bit. */
+/* Launch mode: 0 = one persistent grid over every beam's work items (the
+ * default), 1 = each beam's own kernel launch on its batch configuration, in
+ * turn (still one CUDA graph with dd_batch_capture).  Beams that each fill
+ * the GPU run faster on their own launches; batches of small beams gain from
+ * the persistent grid.  dd_batch_autotune times both and keeps the faster.
+ * Setting the mode drops a captured graph. */
+DD_API int dd_batch_set_launch_mode(dd_batch *batch, int32_t per_beam);
+DD_API int dd_batch_launch_mode(const dd_batch *batch, int32_t *per_beam);
+
+/* Tile configuration beam `beam` runs in the batch (9 or 5 under the mixed
+ * configuration 9, else the batch's), -1 if it runs the generic kernel by
+ * its own launch.  A plan set to that configuration alone (dd_plan_set_tile)
+ * reproduces the beam's batched output bit for bit.  In the per-beam launch
+ * mode every beam with kernel 5 tables runs kernel 5; in the persistent grid
+ * only those whose tables fit three blocks per SM. */
 DD_API int dd_batch_beam_config(const dd_batch *batch, int32_t beam, int32_t *config);
 
 /* Choose the persistent launch's tile configuration (0-6, dd_plan_set_tile's

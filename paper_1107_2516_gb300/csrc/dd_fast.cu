@@ -854,6 +854,7 @@ struct dd_batch {
     dd::LaneLaunch *d_lbeams = nullptr, *h_lbeams = nullptr; // the same for kernel 3 configurations
     dd::ShareLaunch *d_sbeams = nullptr, *h_sbeams = nullptr; // kernel 5 beams of the mixed configuration
     std::vector<int> kind;                 // mixed configuration: 1 = the beam runs kernel 5
+    bool per_beam = false;                 // launch mode: each beam's own kernel launch instead of one persistent grid
     unsigned int *d_counter = nullptr;
     int *d_err = nullptr;
     int bar_off = 0;
@@ -934,7 +935,10 @@ static int batch_build(dd_batch *B, int k)
             bar_off = std::max(bar_off, fp(p)->sh[kMixedShare].bar_off);
         }
     }
-    if (k == kMixedCfg) {
+    if (k == kMixedCfg && B->per_beam) {
+        // own launches: every beam with kernel 5 tables runs kernel 5
+        for (int i : order) B->kind[i] = fp(B->plans[i])->sh[kMixedShare].ok ? 1 : 0;
+    } else if (k == kMixedCfg) {
         // keep the shape's resident blocks per SM: the kernel 5 beams with the
         // largest shared-memory layouts go back to kernel 3 until they fit
         constexpr int nbar = kStages + kShareCfg[kMixedShare].ns;
@@ -993,7 +997,18 @@ static int batch_enqueue(dd_batch *B, const void *const *ins, const int64_t *pit
     int rc = batch_prepare(B);
     if (rc) return rc;
     std::vector<int> own(B->sep);
-    if (B->cfg >= kNumFastCfg) {
+    if (B->per_beam && B->cfg >= 0) {
+        // each beam's single-plan kernel on its batch configuration, in turn
+        for (int i : B->k2) {
+            dd_plan *p = B->plans[i];
+            FastPlan *f = fp(p);
+            if (((uintptr_t)ins[i] & 15u) || (pitches[i] % f->al))
+                return set_error(DD_ERR_ARG, "beam %d: input rows must be 16-byte aligned in a batch", i);
+            const int k = B->cfg != kMixedCfg ? B->cfg : B->kind[i] ? kMixedCfg : kNumFastCfg + kMixedLane;
+            rc = fast_run(p, k, f->dgroup, ins[i], pitches[i], outs[i], s);
+            if (rc) return rc;
+        }
+    } else if (B->cfg >= kNumFastCfg) {
         const bool mixed = B->cfg == kMixedCfg;
         const int kl = mixed ? kMixedLane : B->cfg - kNumFastCfg;
         for (int i : B->k2) {
@@ -1234,24 +1249,30 @@ int dd_batch_autotune(dd_batch *B, const void *const *ins, const int64_t *pitche
     std::vector<int> cfgs;
     for (int k = 0; k < kLaneEnd; ++k) cfgs.push_back(k);
     cfgs.push_back(kMixedCfg);
+    bool bpb = B->per_beam;
     for (int k : cfgs) {
-        if (rc != DD_OK) break;
         bool all = true;
         for (int i = 0; i < (int)B->plans.size(); ++i) {
             const FastPlan *f = fp(B->plans[i]);
             if (f && !batch_geom(f, k).ok) all = false;
         }
         if (!all) continue;
-        rc = batch_build(B, k);
-        if (!rc) rc = batch_enqueue(B, ins, pitches, outs, s);           // warm-up
-        if (!rc) { cudaEventRecord(e0, s); rc = batch_enqueue(B, ins, pitches, outs, s); cudaEventRecord(e1, s); }
-        if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(DD_ERR_CUDA, "autotune sync");
-        float ms = 0.f;
-        if (!rc) cudaEventElapsedTime(&ms, e0, e1);
-        if (!rc && ms < best) { best = ms; bk = k; }
+        // the persistent grid, and (kernel 3 and the mixed configuration) each beam's own launch
+        for (int pb = 0; pb < (k >= kNumFastCfg ? 2 : 1) && rc == DD_OK; ++pb) {
+            B->per_beam = pb == 1;
+            rc = batch_build(B, k);
+            if (!rc) rc = batch_enqueue(B, ins, pitches, outs, s);           // warm-up
+            if (!rc) { cudaEventRecord(e0, s); rc = batch_enqueue(B, ins, pitches, outs, s); cudaEventRecord(e1, s); }
+            if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = set_error(DD_ERR_CUDA, "autotune sync");
+            float ms = 0.f;
+            if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+            if (!rc && ms < best) { best = ms; bk = k; bpb = pb == 1; }
+        }
+        if (rc != DD_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    B->per_beam = bpb;
     if (rc) return rc;
     if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
     if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
@@ -1267,6 +1288,24 @@ int dd_batch_set_config(dd_batch *B, int32_t config)
     if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
     if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
     return batch_build(B, config);
+}
+
+int dd_batch_set_launch_mode(dd_batch *B, int32_t per_beam)
+{
+    if (!B) return set_error(DD_ERR_ARG, "batch is NULL");
+    if (per_beam != 0 && per_beam != 1) return set_error(DD_ERR_ARG, "launch mode must be 0 or 1");
+    cudaDeviceSynchronize();
+    if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+    if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+    B->per_beam = per_beam == 1;
+    return batch_build(B, B->cfg);
+}
+
+int dd_batch_launch_mode(const dd_batch *B, int32_t *per_beam)
+{
+    if (!B || !per_beam) return set_error(DD_ERR_ARG, "NULL argument");
+    *per_beam = B->per_beam ? 1 : 0;
+    return DD_OK;
 }
 
 int dd_batch_beam_config(const dd_batch *B, int32_t beam, int32_t *config)

@@ -31,6 +31,7 @@ EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "d
            "dd_stats_f32_noalloc", "dd_last_error", "dd_version",
            "dd_batch_create", "dd_batch_destroy", "dd_batch_execute", "dd_batch_capture",
            "dd_batch_launch", "dd_batch_results", "dd_batch_autotune", "dd_batch_info", "dd_batch_set_config", "dd_batch_beam_config",
+           "dd_batch_set_launch_mode", "dd_batch_launch_mode",
            "dd_server_create", "dd_server_destroy", "dd_server_add_beam", "dd_server_remove_beam",
            "dd_server_submit", "dd_server_poll", "dd_server_candidates", "dd_server_beam_info",
            "dd_server_memory", "dd_subband_plan_create", "dd_subband_plan_destroy",
@@ -101,6 +102,8 @@ def load(path: Optional[str] = None):
             "dd_batch_info": (C.c_int, [vp, C.POINTER(i32), P64, C.POINTER(i32)]),
             "dd_batch_set_config": (C.c_int, [vp, i32]),
             "dd_batch_beam_config": (C.c_int, [vp, i32, C.POINTER(i32)]),
+            "dd_batch_set_launch_mode": (C.c_int, [vp, i32]),
+            "dd_batch_launch_mode": (C.c_int, [vp, C.POINTER(i32)]),
             "dd_server_create": (C.c_int, [i64, i32, i64, C.POINTER(vp)]),
             "dd_server_destroy": (C.c_int, [vp]),
             "dd_server_add_beam": (C.c_int, [vp, i32, f64, f64, f64, vp, i32, vp, i32, f64, i32, i64,
@@ -443,6 +446,16 @@ class Batch:
 
     def set_config(self, config):
         dd_batch_set_config(self.handle, config)
+
+    @property
+    def per_beam(self):
+        """True if the batch runs each beam's own launch instead of one persistent grid."""
+        c = C.c_int32()
+        _check(load().dd_batch_launch_mode(self.handle, C.byref(c)))
+        return bool(c.value)
+
+    def set_launch_mode(self, per_beam: bool):
+        _check(load().dd_batch_set_launch_mode(self.handle, 1 if per_beam else 0))
 
     def beam_config(self, beam):
         """Tile configuration beam `beam` runs in the persistent launch (-1: its own launch)."""

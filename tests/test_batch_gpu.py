@@ -59,14 +59,18 @@ def _bufs(data, plans):
     return ins, [pitch for _, _, pitch in data], outs
 
 
-@pytest.mark.parametrize("config", [None, 1, 5, 3, 9])
-def test_batch_matches_single_plans_and_graph(beams, config):
+@pytest.mark.parametrize("config,per_beam", [(None, False), (1, False), (5, False), (3, False), (9, False),
+                                             (9, True), (5, True)])
+def test_batch_matches_single_plans_and_graph(beams, config, per_beam):
     # default configuration (the mixed kernel 5 / kernel 3 one), a kernel 2
-    # shape, kernel 3 shapes
+    # shape, kernel 3 shapes; one persistent grid or each beam's own launch
     plans = _plans(beams)
     batch = dd.Batch(plans)
     if config is not None:
         batch.set_config(config)
+    if per_beam:
+        batch.set_launch_mode(True)
+    assert batch.per_beam == per_beam
     cfg, nitems, nsep = batch.info
     assert cfg == (9 if config is None else config) and nitems > 0 and nsep == 0
     for i, p in enumerate(plans):
