@@ -71,6 +71,35 @@ def whole_job_rate(units_per_rank: int, world: int, seconds: float) -> float:
     return units_per_rank * world / seconds
 
 
+def share_words(d: np.ndarray, foff: float, db: int, tile: int, cs: int = 4) -> int:
+    """Shared-memory words one kernel 5 launch moves, from the plan's delay
+    table d [ndm][nchans]: per (DM block of db trials, subband of cs channels,
+    time tile) stage 1 reads cs words and writes one for every partial sum
+    (each delay pattern's sums cover its trials' reference-delay span plus the
+    tile), and stage 2 reads one word per trial and sample."""
+    ndm, nch = d.shape
+    nblk, nsub = -(-ndm // db), nch // cs
+    rows = np.minimum(np.arange(nblk * db), ndm - 1)      # the ragged last block repeats the last trial
+    dd = d[rows].astype(np.int64).reshape(nblk, db, nsub, cs)
+    ref = dd[..., 0] if foff < 0 else dd[..., cs - 1]      # the subband's highest frequency
+    rel = dd - ref[..., None]
+    key = np.zeros(ref.shape, np.int64)
+    for c in range(cs):                                   # relative delays as one key (each < 2^15)
+        key = key * (1 << 15) + rel[..., c]
+    b = np.broadcast_to(np.arange(nblk)[:, None, None], key.shape).ravel()
+    s = np.broadcast_to(np.arange(nsub)[None, None, :], key.shape).ravel()
+    k, r = key.ravel(), ref.ravel()
+    order = np.lexsort((r, k, s, b))
+    b, s, k, r = b[order], s[order], k[order], r[order]
+    start = np.ones(len(k), bool)
+    start[1:] = (b[1:] != b[:-1]) | (s[1:] != s[:-1]) | (k[1:] != k[:-1])
+    first = np.flatnonzero(start)
+    last = np.append(first[1:], len(k)) - 1
+    stage1 = int(np.sum(r[last] - r[first] + tile)) * (cs + 1)
+    stage2 = nblk * nsub * db * tile
+    return stage1 + stage2
+
+
 def _pulses(wl, nout, seed):
     return synth.draw_pulses(16, 0.0, wl.dm_list[-1], 1, 32, 8.0, 20.0, nout - 32, wl.nchans, seed)
 
@@ -293,6 +322,7 @@ def run_ours(args, rank, world, local_rank):
 
     kernel_id = plan.kernel
     tile = plan.tile if kernel_id in (2, 3, 4, 5) else None
+    d_plan = plan.delays() if kernel_id == 5 else None
     plan.close()
     del out, xin
     if rank != 0:
@@ -322,9 +352,20 @@ def run_ours(args, rank, world, local_rank):
     if kernel_id == 5:
         # kernel 5 shares each 4-channel subband's partial sums between the DM
         # trials of a block with the same relative delays: `achieved` counts
-        # the brute-force-equivalent channel-adds of the exact result
+        # the brute-force-equivalent channel-adds of the exact result; the
+        # bound it meets is the shared-memory data path, here against the words
+        # its two stages move
         roof["note"] = ("kernel 5: exact shared subband partial sums; achieved = brute-force-equivalent "
                         "channel-adds (the sum is identical; fewer adds are executed)")
+        _, ns, nd, nw = TILE_CONFIGS[tile[0]]
+        ntile = -(-nout // (32 * ns))
+        words = share_words(d_plan, wl.foff, nd * nw, 32 * ns) * ntile
+        lds_peak = sm * 32 * sm_max * 1e6 / 1e9
+        aw = words / (ker_ms / 1e3) / 1e9
+        roof["secondary"] = {"bound": "shared-memory words", "achieved": aw, "peak": lds_peak,
+                             "unit": "Gword/s", "frac": aw / lds_peak,
+                             "words_per_output": words / (wl.ndm * nout),
+                             "peak_basis": f"{sm} SMs x 32 banks x {sm_max:.0f} MHz"}
     if kernel_id == 3:
         # kernel 3 loads one shared-memory word per add: the shared-memory data
         # path (32 words/clk/SM, 4 B x 32 banks) caps it at a quarter of the add peak

@@ -1,0 +1,48 @@
+"""Host-side accounting of bench.py (no GPU): the shared-memory words one
+kernel 5 launch moves, which its roofline line divides by the kernel time,
+against a plain loop over DM blocks and subbands."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import oracle  # noqa: E402
+
+
+def _words_loop(d, foff, db, tile, cs=4):
+    ndm, nch = d.shape
+    total = 0
+    for b in range(-(-ndm // db)):
+        trials = [min(b * db + j, ndm - 1) for j in range(db)]
+        for s in range(nch // cs):
+            spans = {}
+            for j in trials:
+                sub = [int(v) for v in d[j, s * cs:(s + 1) * cs]]
+                ref = sub[0] if foff < 0 else sub[-1]
+                key = tuple(v - ref for v in sub)
+                lo, hi = spans.get(key, (ref, ref))
+                spans[key] = (min(lo, ref), max(hi, ref))
+            total += sum(hi - lo + tile for lo, hi in spans.values()) * (cs + 1) + db * tile
+    return total
+
+
+@pytest.mark.parametrize("foff", [-0.39, 0.39])
+@pytest.mark.parametrize("db,tile", [(8, 64), (12, 32)])
+def test_share_words_matches_loop(foff, db, tile):
+    # 16 channels, 37 trials (ragged last block), both band orientations
+    fch1 = 150.0 if foff < 0 else 150.0 - 15 * abs(foff)
+    dms = [0.7 * i for i in range(37)]
+    d, _ = oracle.delays(16, fch1, foff, 327.68e-6, dms)
+    d = np.asarray(d)
+    assert bench.share_words(d, foff, db, tile) == _words_loop(d, foff, db, tile)
+
+
+def test_share_words_single_pattern():
+    # all trials with the same delays (DM 0): one pattern of span 0 per subband
+    d = np.zeros((5, 8), np.int32)
+    assert bench.share_words(d, -1.0, 4, 32) == 2 * 2 * ((32 * 5) + 4 * 32)
