@@ -6,8 +6,8 @@
 // with the smallest delay.  DM trials of a block whose relative delays
 // r(c) within a subband coincide (a "pattern") share one partial sum: the
 // result is exactly the brute-force sum (same integer delays; FP32 rounding
-// order differs), computed with (#patterns x CS + #trials) shared-memory
-// words per subband and output tile instead of #trials x CS.
+// order differs), computed with about #patterns x (CS + 1) + #trials
+// shared-memory words per subband and output sample instead of #trials x CS.
 //
 // Block = NW warps on a tile of 32*TI samples (lanes interleaved as kernel 3)
 // and DR*NW DM trials.  Per subband (one TMA stage: its CS input rows and
@@ -22,14 +22,14 @@
 // One __syncthreads per subband: stage 1 of subband s+1 writes the other P
 // buffer while stage 2 of s reads this one; each warp takes its trials'
 // offsets into registers during stage 1 (the stage's record may be reused by
-// the next TMA copy before stage 2 ends).  The input ring has two stages
-// (NS) stages: NS - 1 subbands' copies are in flight while one is summed.
+// the next TMA copy before stage 2 ends).  The input ring has NS stages:
+// NS - 1 subbands' copies are in flight while one is summed.  The tile body
+// (share_tile) serves the one-plan kernel and the persistent batch kernel.
 #pragma once
 
 #include "dd_lane_impl.cuh"
 
 namespace dd {
-
 
 // Table record of one (DM block, subband), int32 (16-byte multiple):
 //   [0 .. DB) q_j (index into P of trial j's t = t0 term) | [DB] E (the
