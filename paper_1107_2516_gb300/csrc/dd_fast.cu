@@ -683,17 +683,22 @@ int fast_execute_host(dd_plan *p, const void *in_host, int64_t pitch, void *in_d
     FastPlan *f = static_cast<FastPlan *>(p->fast);
     if (!f || ((uintptr_t)in_dev & 15u) || (pitch % f->al)) return kNotPipelined;
     const int k = f->active;
-    int tile;
+    int tile, nblk;
     int64_t reach;
     if (k >= kShareBeg) {
         tile = 32 * kShareCfg[k - kShareBeg].ti;
         reach = f->sh[k - kShareBeg].reach;
+        nblk = f->sh[k - kShareBeg].nblk;
     } else if (k >= kNumFastCfg && k < kLaneEnd) {
         tile = 32 * f->lane[k - kNumFastCfg].ti;
         reach = f->lane[k - kNumFastCfg].reach;
+        nblk = f->lane[k - kNumFastCfg].nblk;
     } else {
         return kNotPipelined;
     }
+    // plans whose grid would fall back to the generic kernel (which reads the
+    // whole input) take the unsplit path
+    if ((p->nsamp_out + tile - 1) / tile * nblk > INT32_MAX) return kNotPipelined;
     cudaError_t e = cudaSuccess;
     if (!f->copy_stream) {
         e = cudaStreamCreateWithFlags(&f->copy_stream, cudaStreamNonBlocking);
