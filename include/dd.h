@@ -268,6 +268,25 @@ DD_API int dd_batch_results(dd_batch *batch, int32_t beam, dd_candidate *cand_ho
 DD_API int dd_batch_autotune(dd_batch *batch, const void *const *in_devs, const int64_t *in_pitches,
                              void *const *out_devs, void *stream);
 
+/* Kernel 5's tables for tile configuration `config` (9-11) of a delay table
+ * delays[ndm][nchans] (dd_plan_info's copy), computed on the host (no device
+ * needed), for inspection and tests.  info[6] receives {1 if the shape can
+ * run the table (at most 16 delay patterns per block and subband) else 0,
+ * DM blocks, subbands, staged row stride rs, largest partial-sum length,
+ * record length kLen}.  If info[0] is 1 and rec_out / base_out are not NULL,
+ * they receive the records int32 [blocks][subbands][kLen] — [0, trials):
+ * each trial's partial-sum index of its first sample; [trials]: the
+ * subband's partial-sum length E; from trials + 4, 8 words per pattern:
+ * {end of its sums in the partial-sum buffer, then per channel c of the
+ * subband the staged element of its first term minus its start} — and the
+ * staged row starts int32 [blocks][nchans] relative to a tile's first
+ * output sample.  foff's sign picks the subband reference channel (the
+ * highest frequency).  DD_ERR_ARG for another configuration or too small a
+ * capacity. */
+DD_API int dd_share_tables(const int32_t *delays, int32_t ndm, int32_t nchans, double foff, int32_t dtype,
+                           int32_t config, int32_t *info, int32_t *rec_out, int64_t rec_cap, int32_t *base_out,
+                           int64_t base_cap);
+
 /* Tile configuration the persistent launch uses (-1 if no beam uses it),
  * number of work items, and number of beams run by their own launch.  A new
  * batch starts with the first of configurations 9, 5, 3, 6, 4, 1, 0, 2 that

@@ -269,25 +269,35 @@ static void free_share(ShareCfgData &c)
 // of its t = t0 term.  c.ok stays false when the channel count is not a
 // multiple of kShCS, a (block, subband) has more than kShNP patterns, or the
 // buffers do not fit three blocks per SM.
+// Kernel 5's tables of shape k for a delay table [D][C] (host only): per
+// (DM block, subband) record (layout of ShareRec) and per (DM block, channel)
+// staged row start; T.ok stays false if a (block, subband) has more than
+// kShNP delay patterns.
+struct ShareTables {
+    std::vector<int32_t> rec, base;
+    int nblk = 0, nsub = 0, rs = 0, pmax = 0, klen = 0;
+    bool ok = false;
+};
+
 template <int DB>
-static int build_share_db(const dd_plan *p, int k, ShareCfgData &c)
+static void share_tables_db(const int32_t *delays, int D, int C, double foff, dd_dtype dtype, int k,
+                            ShareTables &T)
 {
-    c = ShareCfgData();
+    T = ShareTables();
     constexpr int CS = kShCS, NP = kShNP;
-    const int TILE = 32 * kShareCfg[k].ti, minb = kShareCfg[k].minb;
+    const int TILE = 32 * kShareCfg[k].ti;
     using R = ShareRecDB<DB>;
-    const int C = p->nchans, D = p->ndm;
-    if (C % CS) return DD_OK;
+    if (C % CS) return;
     const int S = C / CS, nblk = (D + DB - 1) / DB;
-    const int AL = elem_align(p->dtype);
+    const int AL = elem_align(dtype);
     std::vector<int32_t> rec((size_t)nblk * S * R::kLen, 0), base((size_t)nblk * C);
     std::vector<int> npat((size_t)nblk * S);
-    auto dl = [&](int dm, int ch) { return p->delays[(size_t)std::min(dm, D - 1) * C + ch]; };
+    auto dl = [&](int dm, int ch) { return delays[(size_t)std::min(dm, D - 1) * C + ch]; };
     long long need = 0;
     int pmax = 0;
     for (int b = 0; b < nblk; ++b)
         for (int s = 0; s < S; ++s) {
-            const int ref = p->foff < 0.0 ? s * CS : s * CS + CS - 1;
+            const int ref = foff < 0.0 ? s * CS : s * CS + CS - 1;
             int dref[DB], pid[DB];
             std::vector<std::array<int, CS>> pats;
             int dmin = INT_MAX;
@@ -296,12 +306,12 @@ static int build_share_db(const dd_plan *p, int k, ShareCfgData &c)
                 dmin = std::min(dmin, dref[j]);
                 std::array<int, CS> r;
                 for (int cc = 0; cc < CS; ++cc) r[cc] = dl(b * DB + j, s * CS + cc) - dref[j];
-                int k = 0;
-                while (k < (int)pats.size() && pats[k] != r) ++k;
-                if (k == (int)pats.size()) pats.push_back(r);
-                pid[j] = k;
+                int q = 0;
+                while (q < (int)pats.size() && pats[q] != r) ++q;
+                if (q == (int)pats.size()) pats.push_back(r);
+                pid[j] = q;
             }
-            if ((int)pats.size() > NP) return DD_OK;
+            if ((int)pats.size() > NP) return;
             int32_t *t = &rec[((size_t)b * S + s) * R::kLen];
             int rowoff[CS];
             for (int cc = 0; cc < CS; ++cc) {
@@ -318,16 +328,16 @@ static int build_share_db(const dd_plan *p, int k, ShareCfgData &c)
             // patterns end to end in P; b_c without the row stride (added once rs is known)
             int poff = 0;
             std::vector<int> plo(pats.size()), pof(pats.size());
-            for (int k = 0; k < (int)pats.size(); ++k) {
+            for (int q = 0; q < (int)pats.size(); ++q) {
                 int lo = INT_MAX, hi = INT_MIN;
                 for (int j = 0; j < DB; ++j)
-                    if (pid[j] == k) { lo = std::min(lo, dref[j] - dmin); hi = std::max(hi, dref[j] - dmin); }
+                    if (pid[j] == q) { lo = std::min(lo, dref[j] - dmin); hi = std::max(hi, dref[j] - dmin); }
                 const int W = hi - lo + TILE;
-                int32_t *pr = t + R::kPat + k * R::kPatLen;
+                int32_t *pr = t + R::kPat + q * R::kPatLen;
                 pr[0] = poff + W;
-                for (int cc = 0; cc < CS; ++cc) pr[1 + cc] = rowoff[cc] + lo + pats[k][cc] - poff;
-                plo[k] = lo;
-                pof[k] = poff;
+                for (int cc = 0; cc < CS; ++cc) pr[1 + cc] = rowoff[cc] + lo + pats[q][cc] - poff;
+                plo[q] = lo;
+                pof[q] = poff;
                 poff += W;
             }
             t[R::kE] = poff;
@@ -337,39 +347,51 @@ static int build_share_db(const dd_plan *p, int k, ShareCfgData &c)
         }
     const int rs = (int)((need + 15) / 16 * 16);
     for (size_t r = 0; r < npat.size(); ++r)
-        for (int k = 0; k < npat[r]; ++k)
-            for (int cc = 0; cc < CS; ++cc) rec[r * R::kLen + R::kPat + k * R::kPatLen + 1 + cc] += cc * rs;
+        for (int q = 0; q < npat[r]; ++q)
+            for (int cc = 0; cc < CS; ++cc) rec[r * R::kLen + R::kPat + q * R::kPatLen + 1 + cc] += cc * rs;
+    T.rec.swap(rec);
+    T.base.swap(base);
+    T.nblk = nblk; T.nsub = S; T.rs = rs; T.pmax = pmax; T.klen = R::kLen;
+    T.ok = true;
+}
+
+static void share_tables(const int32_t *delays, int D, int C, double foff, dd_dtype dtype, int k, ShareTables &T)
+{
+    switch (kShareCfg[k].dr * kShareCfg[k].nw) {
+    case 32: share_tables_db<32>(delays, D, C, foff, dtype, k, T); break;
+    case 48: share_tables_db<48>(delays, D, C, foff, dtype, k, T); break;
+    default: T = ShareTables(); break;
+    }
+}
+
+static int build_share(const dd_plan *p, int k, ShareCfgData &c)
+{
+    c = ShareCfgData();
+    ShareTables T;
+    share_tables(p->delays.data(), p->ndm, p->nchans, p->foff, p->dtype, k, T);
+    if (!T.ok) return DD_OK;
     const size_t eb = in_elem_bytes(p->dtype);
     // shared memory: input stages | records | 2 partial-sum buffers | mbarriers;
     // the shape's target blocks per SM if it fits, else fewer (>= 2)
-    const int nis = kShareCfg[k].ns;
-    const int pm4 = (pmax + 3) / 4 * 4;
-    const size_t rows_b = (size_t)nis * CS * rs * eb, rec_b = (size_t)nis * R::kLen * 4;
+    const int nis = kShareCfg[k].ns, minb = kShareCfg[k].minb;
+    const int pm4 = (T.pmax + 3) / 4 * 4;
+    const size_t rows_b = (size_t)nis * kShCS * T.rs * eb, rec_b = (size_t)nis * T.klen * 4;
     const size_t bar_off = (rows_b + rec_b + (size_t)2 * pm4 * 4 + 15) / 16 * 16;
     const size_t need_b = bar_off + nis * sizeof(uint64_t);
     bool fits = false;
     for (int nb = minb; nb >= std::min(minb, 2) && !fits; --nb)
         fits = need_b <= std::min<size_t>(p->smem_optin, (228 * 1024) / nb - 1024) - 1024;
     if (!fits) return DD_OK;
-    c.reach = (int64_t)*std::max_element(base.begin(), base.end()) + rs;
-    c.nblk = nblk; c.nsub = S; c.rs = rs; c.pmax = pm4; c.bar_off = (int)bar_off;
+    c.reach = (int64_t)*std::max_element(T.base.begin(), T.base.end()) + T.rs;
+    c.nblk = T.nblk; c.nsub = T.nsub; c.rs = T.rs; c.pmax = pm4; c.bar_off = (int)bar_off;
     c.smem = need_b;
-    cudaError_t e = cudaMalloc(&c.d_rec, rec.size() * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&c.d_base, base.size() * 4);
-    if (e == cudaSuccess) e = cudaMemcpy(c.d_rec, rec.data(), rec.size() * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(c.d_base, base.data(), base.size() * 4, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMalloc(&c.d_rec, T.rec.size() * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_base, T.base.size() * 4);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_rec, T.rec.data(), T.rec.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_base, T.base.data(), T.base.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { free_share(c); return cuda_fail(e, "kernel 5 tables"); }
     c.ok = true;
     return DD_OK;
-}
-
-static int build_share(const dd_plan *p, int k, ShareCfgData &c)
-{
-    switch (kShareCfg[k].dr * kShareCfg[k].nw) {
-    case 32: return build_share_db<32>(p, k, c);
-    case 48: return build_share_db<48>(p, k, c);
-    default: c = ShareCfgData(); return DD_OK;
-    }
 }
 
 static void free_cfg(FastCfgData &c)
@@ -1117,6 +1139,30 @@ static int batch_enqueue(dd_batch *B, const void *const *ins, const int64_t *pit
 using namespace dd;
 
 extern "C" {
+
+int dd_share_tables(const int32_t *delays, int32_t ndm, int32_t nchans, double foff, int32_t dtype,
+                    int32_t config, int32_t *info, int32_t *rec_out, int64_t rec_cap, int32_t *base_out,
+                    int64_t base_cap)
+{
+    if (!delays || !info || ndm < 1 || nchans < 1) return set_error(DD_ERR_ARG, "bad table arguments");
+    if (dtype != DD_F32 && dtype != DD_U8 && dtype != DD_F16) return set_error(DD_ERR_ARG, "bad dtype %d", dtype);
+    if (config < kShareBeg || config >= kShareBeg + kNumShareCfg)
+        return set_error(DD_ERR_ARG, "configuration %d is not a kernel 5 shape", config);
+    ShareTables T;
+    share_tables(delays, ndm, nchans, foff, (dd_dtype)dtype, config - kShareBeg, T);
+    info[0] = T.ok ? 1 : 0;
+    info[1] = T.nblk; info[2] = T.nsub; info[3] = T.rs; info[4] = T.pmax; info[5] = T.klen;
+    if (!T.ok) return DD_OK;
+    if (rec_out) {
+        if (rec_cap < (int64_t)T.rec.size()) return set_error(DD_ERR_ARG, "record buffer too small");
+        memcpy(rec_out, T.rec.data(), T.rec.size() * 4);
+    }
+    if (base_out) {
+        if (base_cap < (int64_t)T.base.size()) return set_error(DD_ERR_ARG, "row-start buffer too small");
+        memcpy(base_out, T.base.data(), T.base.size() * 4);
+    }
+    return DD_OK;
+}
 
 int dd_batch_create(dd_plan *const *plans, int32_t nplans, dd_batch **out)
 {

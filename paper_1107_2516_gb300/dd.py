@@ -31,7 +31,7 @@ EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "d
            "dd_stats_f32_noalloc", "dd_last_error", "dd_version",
            "dd_batch_create", "dd_batch_destroy", "dd_batch_execute", "dd_batch_capture",
            "dd_batch_launch", "dd_batch_results", "dd_batch_autotune", "dd_batch_info", "dd_batch_set_config", "dd_batch_beam_config",
-           "dd_batch_set_launch_mode", "dd_batch_launch_mode",
+           "dd_batch_set_launch_mode", "dd_batch_launch_mode", "dd_share_tables",
            "dd_server_create", "dd_server_destroy", "dd_server_add_beam", "dd_server_remove_beam",
            "dd_server_submit", "dd_server_poll", "dd_server_candidates", "dd_server_beam_info",
            "dd_server_memory", "dd_subband_plan_create", "dd_subband_plan_destroy",
@@ -104,6 +104,7 @@ def load(path: Optional[str] = None):
             "dd_batch_beam_config": (C.c_int, [vp, i32, C.POINTER(i32)]),
             "dd_batch_set_launch_mode": (C.c_int, [vp, i32]),
             "dd_batch_launch_mode": (C.c_int, [vp, C.POINTER(i32)]),
+            "dd_share_tables": (C.c_int, [vp, i32, i32, f64, i32, i32, vp, vp, i64, vp, i64]),
             "dd_server_create": (C.c_int, [i64, i32, i64, C.POINTER(vp)]),
             "dd_server_destroy": (C.c_int, [vp]),
             "dd_server_add_beam": (C.c_int, [vp, i32, f64, f64, f64, vp, i32, vp, i32, f64, i32, i64,
@@ -333,6 +334,25 @@ def dd_batch_info(batch: int):
 
 def dd_batch_set_config(batch: int, config: int) -> None:
     _check(load().dd_batch_set_config(batch, int(config)))
+
+
+def dd_share_tables(delays: np.ndarray, foff: float, dtype: int, config: int):
+    """Kernel 5's tables (host only) for a delay table [ndm][nchans]: None if the
+    shape cannot run it, else dict(rec [blocks][subbands][kLen], base
+    [blocks][nchans], rs, pmax, klen)."""
+    d = np.ascontiguousarray(delays, dtype=np.int32)
+    ndm, nch = d.shape
+    info = np.zeros(6, np.int32)
+    _check(load().dd_share_tables(_ptr(d), ndm, nch, float(foff), int(dtype), int(config), _ptr(info), None, 0,
+                                  None, 0))
+    if not info[0]:
+        return None
+    nblk, nsub, rs, pmax, klen = (int(v) for v in info[1:])
+    rec = np.empty((nblk, nsub, klen), np.int32)
+    base = np.empty((nblk, nch), np.int32)
+    _check(load().dd_share_tables(_ptr(d), ndm, nch, float(foff), int(dtype), int(config), _ptr(info), _ptr(rec),
+                                  rec.size, _ptr(base), base.size))
+    return {"rec": rec, "base": base, "rs": rs, "pmax": pmax, "klen": klen}
 
 
 def dd_batch_beam_config(batch: int, beam: int) -> int:

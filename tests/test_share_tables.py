@@ -1,0 +1,116 @@
+"""Kernel 5's tables as the library builds them (dd_share_tables, host only, no
+GPU): the two stages of the kernel executed in numpy from those tables give
+the oracle's brute-force sums, and every index stays inside the buffer it
+addresses.
+
+Stage 1: for subband s of DM block b and the time tile at t0, P[e] (e < E)
+sums the subband's 4 staged input rows at the staged element b_c + e of the
+pattern e belongs to; the rows hold input columns t0 + base[b][c] onwards,
+as many as the input has (the rest of a staged row is never written: NaN
+here).  Stage 2: trial j adds P[q_j + i] to its output sample t0 + i."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1107_2516_gb300 as dd
+from paper_1107_2516_gb300 import build as ddbuild
+from paper_1107_2516_gb300 import dd as ddc
+
+CS = 4
+SHAPES = {9: (512, 32), 10: (256, 32), 11: (512, 48)}     # config: (tile, trials per block)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    ddbuild.build()
+    dd.load()
+
+
+def emulate(x, nsamp, d, foff, dtype, config):
+    """The kernel's sums from the library's tables (None if the shape cannot run)."""
+    t = ddc.dd_share_tables(d, foff, dtype, config)
+    if t is None:
+        return None
+    rec, base, rs = t["rec"], t["base"], t["rs"]
+    tile, db = SHAPES[config]
+    ndm, nch = d.shape
+    nblk, nsub, _ = rec.shape
+    al = 16 if dtype == dd.DD_U8 else 4
+    nsamp_al = (nsamp + al - 1) // al * al
+    nout = nsamp - int(d.max())
+    ntile = -(-nout // tile)
+    out = np.full((nblk * db, ntile * tile), np.nan)
+    for b in range(nblk):
+        for j in range(ntile):
+            t0 = j * tile
+            acc = np.zeros((db, tile))
+            for s in range(nsub):
+                stage = np.full(CS * rs, np.nan)
+                for c in range(CS):
+                    g = t0 + int(base[b, s * CS + c])
+                    n = max(0, min(rs, nsamp_al - g))
+                    stage[c * rs:c * rs + n] = x[s * CS + c, g:g + n]
+                r = rec[b, s]
+                E = int(r[db])
+                pats = r[db + 4:].reshape(-1, 8)
+                ends = pats[:, 0]
+                e = np.arange(E)
+                p = np.searchsorted(ends[ends > 0], e, side="right")
+                assert E == int(ends[p.max()]) and np.all(np.diff(ends[:p.max() + 1]) > 0)
+                P = np.zeros(E)
+                for c in range(CS):
+                    idx = pats[p, 1 + c] + e
+                    # channel c's term comes from channel c's staged row
+                    assert idx.min() >= c * rs and idx.max() < (c + 1) * rs
+                    P += stage[idx]
+                q = r[:db].astype(np.int64)
+                assert q.min() >= 0 and q.max() + tile <= E
+                acc += P[q[:, None] + np.arange(tile)[None, :]]
+            out[b * db:(b + 1) * db, t0:t0 + tile] = acc
+    return out[:ndm, :nout]
+
+
+CASES = [
+    # nchans, fch1, foff, tsamp, DMs, nsamp, dtype (ragged last block and tile in each)
+    (128, 150.0, -0.0234375, 163.84e-6, [0.1 * i for i in range(60)], 2700, "f32"),       # 11-15 patterns
+    (96, 150.0 - 95 * 0.0234375, 0.0234375, 163.84e-6, [0.1 * i for i in range(50)], 2300, "u8"),  # ascending
+    (256, 150.0, -0.046875, 163.84e-6, [0.05 * i for i in range(100)], 3000, "f32"),      # 13 / 17 patterns
+]
+
+
+@pytest.mark.parametrize("config", [9, 10, 11])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_kernel5_tables_reproduce_brute_force(case, config):
+    nch, fch1, foff, ts, dms, nsamp, dt = CASES[case]
+    d, m = oracle.delays(nch, fch1, foff, ts, dms)
+    d = np.asarray(d)
+    al = 16 if dt == "u8" else 4
+    pitch = (nsamp + al - 1) // al * al + al
+    x = synth.noise_f32(nch, nsamp, 11 + case, pitch=pitch)
+    if dt == "u8":
+        x = synth.quantize_u8(x)
+    got = emulate(x.astype(np.float64), nsamp, d, foff, dd.DD_U8 if dt == "u8" else dd.DD_F32, config)
+    if got is None:
+        # more than 16 delay patterns in some (block, subband): the shape refuses the plan
+        pytest.skip("shape unavailable for this plan")
+    ref = oracle.dedisperse(x, d, nsamp - m)
+    assert not np.isnan(got).any()
+    if dt == "u8":
+        assert np.array_equal(got.astype(np.int64), ref)
+    else:
+        assert np.max(np.abs(got - ref)) <= 1e-9 * nch
+
+
+def test_kernel5_tables_refuse_many_patterns():
+    # the small workload's 128 channels and 0.1 DM steps give 29 patterns per
+    # (32-trial block, subband): more than the 16 the records hold
+    wl = synth.workload("small_f32")
+    d, _ = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
+    assert ddc.dd_share_tables(np.asarray(d), wl.foff, dd.DD_F32, 9) is None
+
+
+def test_kernel5_tables_bad_config():
+    d = np.zeros((4, 8), np.int32)
+    with pytest.raises(dd.DDError):
+        ddc.dd_share_tables(d, -1.0, dd.DD_F32, 5)
