@@ -268,6 +268,16 @@ DD_API int dd_batch_results(dd_batch *batch, int32_t beam, dd_candidate *cand_ho
 DD_API int dd_batch_autotune(dd_batch *batch, const void *const *in_devs, const int64_t *in_pitches,
                              void *const *out_devs, void *stream);
 
+/* dd_process_host's pipeline schedule (host only) for nsamp_out outputs in
+ * tiles of `tile` samples whose input columns lie below the tile's first
+ * sample + reach, with rows of `pitch` elements: *n (<= 8) chunks; chunk c
+ * copies input columns up to col_end[c] (non-decreasing; the last is the
+ * pitch), then de-disperses tiles up to tile_end[c] (the last is every
+ * tile).  col_end and tile_end hold at least 8 entries.  DD_ERR_ARG for
+ * non-positive sizes. */
+DD_API int dd_host_chunk_schedule(int64_t nsamp_out, int64_t pitch, int32_t tile, int64_t reach,
+                                  int64_t *col_end, int64_t *tile_end, int32_t *n);
+
 /* Kernel 5's tables for tile configuration `config` (9-11) of a delay table
  * delays[ndm][nchans] (dd_plan_info's copy), computed on the host (no device
  * needed), for inspection and tests.  info[6] receives {1 if the shape can

@@ -694,6 +694,26 @@ int fast_execute(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStrea
     return fast_run(p, f->active, f->dgroup, in, pitch, out, s);
 }
 
+// Schedule of the pipelined host path for nsamp_out outputs in tiles of
+// `tile` samples whose inputs lie below t0 + reach: up to kHostChunks chunks,
+// chunk c copies input columns up to col_end[c] (multiples of 64, the last
+// one the whole pitch) and then launches tiles up to tile_end[c].  Returns
+// the number of chunks.
+static int host_chunks(int64_t nsamp_out, int64_t pitch, int tile, int64_t reach, int64_t *col_end,
+                       int64_t *tile_end)
+{
+    const int64_t ntile = (nsamp_out + tile - 1) / tile;
+    const int nch = (int)std::min<int64_t>(kHostChunks, ntile);
+    int64_t col = 0;
+    for (int c = 0; c < nch; ++c) {
+        tile_end[c] = ntile * (c + 1) / nch;
+        const int64_t need = c == nch - 1 ? pitch : std::min<int64_t>(pitch, (tile_end[c] * tile + reach + 63) / 64 * 64);
+        col = std::max(col, need);
+        col_end[c] = col;
+    }
+    return nch;
+}
+
 // dd_process_host with kernels 3 and 5: the input goes to the device in
 // kHostChunks column chunks on the plan's copy stream, and after chunk k the
 // output tiles whose input it completes run on `s` while the next chunk is
@@ -729,16 +749,15 @@ int fast_execute_host(dd_plan *p, const void *in_host, int64_t pitch, void *in_d
         if (e != cudaSuccess) return cuda_fail(e, "copy stream");
     }
     const size_t eb = in_elem_bytes(p->dtype);
-    const int64_t ntile = (p->nsamp_out + tile - 1) / tile;
-    const int nch = (int)std::min<int64_t>(kHostChunks, ntile);
     // the copies wait for earlier work on `s` (it may still read the staging buffer)
     e = cudaEventRecord(f->copy_ev[kHostChunks], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(f->copy_stream, f->copy_ev[kHostChunks], 0);
     if (e != cudaSuccess) return cuda_fail(e, "order input copy");
+    int64_t col_end[kHostChunks], tile_end[kHostChunks];
+    const int nch = host_chunks(p->nsamp_out, pitch, tile, reach, col_end, tile_end);
     int64_t col = 0, tlo = 0;
     for (int c = 0; c < nch; ++c) {
-        const int64_t thi = ntile * (c + 1) / nch;
-        int64_t end = c == nch - 1 ? pitch : std::min<int64_t>(pitch, (thi * tile + reach + 63) / 64 * 64);
+        const int64_t thi = tile_end[c], end = col_end[c];
         if (end > col) {
             e = cudaMemcpy2DAsync(static_cast<char *>(in_dev) + col * eb, (size_t)pitch * eb,
                                   static_cast<const char *>(in_host) + col * eb, (size_t)pitch * eb,
@@ -1139,6 +1158,15 @@ static int batch_enqueue(dd_batch *B, const void *const *ins, const int64_t *pit
 using namespace dd;
 
 extern "C" {
+
+int dd_host_chunk_schedule(int64_t nsamp_out, int64_t pitch, int32_t tile, int64_t reach, int64_t *col_end,
+                           int64_t *tile_end, int32_t *n)
+{
+    if (!col_end || !tile_end || !n || nsamp_out < 1 || tile < 1 || reach < 0 || pitch < 1)
+        return set_error(DD_ERR_ARG, "bad schedule arguments");
+    *n = host_chunks(nsamp_out, pitch, tile, reach, col_end, tile_end);
+    return DD_OK;
+}
 
 int dd_share_tables(const int32_t *delays, int32_t ndm, int32_t nchans, double foff, int32_t dtype,
                     int32_t config, int32_t *info, int32_t *rec_out, int64_t rec_cap, int32_t *base_out,

@@ -32,6 +32,7 @@ EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "d
            "dd_batch_create", "dd_batch_destroy", "dd_batch_execute", "dd_batch_capture",
            "dd_batch_launch", "dd_batch_results", "dd_batch_autotune", "dd_batch_info", "dd_batch_set_config", "dd_batch_beam_config",
            "dd_batch_set_launch_mode", "dd_batch_launch_mode", "dd_share_tables",
+           "dd_host_chunk_schedule",
            "dd_server_create", "dd_server_destroy", "dd_server_add_beam", "dd_server_remove_beam",
            "dd_server_submit", "dd_server_poll", "dd_server_candidates", "dd_server_beam_info",
            "dd_server_memory", "dd_subband_plan_create", "dd_subband_plan_destroy",
@@ -105,6 +106,7 @@ def load(path: Optional[str] = None):
             "dd_batch_set_launch_mode": (C.c_int, [vp, i32]),
             "dd_batch_launch_mode": (C.c_int, [vp, C.POINTER(i32)]),
             "dd_share_tables": (C.c_int, [vp, i32, i32, f64, i32, i32, vp, vp, i64, vp, i64]),
+            "dd_host_chunk_schedule": (C.c_int, [i64, i64, i32, i64, vp, vp, C.POINTER(i32)]),
             "dd_server_create": (C.c_int, [i64, i32, i64, C.POINTER(vp)]),
             "dd_server_destroy": (C.c_int, [vp]),
             "dd_server_add_beam": (C.c_int, [vp, i32, f64, f64, f64, vp, i32, vp, i32, f64, i32, i64,
@@ -334,6 +336,16 @@ def dd_batch_info(batch: int):
 
 def dd_batch_set_config(batch: int, config: int) -> None:
     _check(load().dd_batch_set_config(batch, int(config)))
+
+
+def dd_host_chunk_schedule(nsamp_out: int, pitch: int, tile: int, reach: int):
+    """dd_process_host's pipeline schedule: (col_end, tile_end) arrays, one entry per chunk."""
+    col = np.zeros(8, np.int64)
+    til = np.zeros(8, np.int64)
+    n = C.c_int32()
+    _check(load().dd_host_chunk_schedule(int(nsamp_out), int(pitch), int(tile), int(reach), _ptr(col),
+                                         _ptr(til), C.byref(n)))
+    return col[:n.value].copy(), til[:n.value].copy()
 
 
 def dd_share_tables(delays: np.ndarray, foff: float, dtype: int, config: int):

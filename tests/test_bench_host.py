@@ -46,3 +46,26 @@ def test_share_words_single_pattern():
     # all trials with the same delays (DM 0): one pattern of span 0 per subband
     d = np.zeros((5, 8), np.int32)
     assert bench.share_words(d, -1.0, 4, 32) == 2 * 2 * ((32 * 5) + 4 * 32)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_pipeline_schedule_covers_every_tile(seed):
+    # dd_process_host's chunks: the tile ranges partition all tiles, the copied
+    # columns only grow and end at the pitch, and every tile launched after
+    # chunk c reads only columns that chunk c's copies have completed
+    from paper_1107_2516_gb300 import build as ddbuild
+    from paper_1107_2516_gb300 import dd as ddc
+    ddbuild.build()
+    rng = np.random.default_rng(seed)
+    for _ in range(200):
+        tile = int(rng.choice([256, 384, 512, 640]))
+        nout = int(rng.integers(1, 40 * tile))
+        reach = int(rng.integers(tile, tile + 30000))
+        pitch = nout + reach - tile + int(rng.integers(0, 64))
+        col, til = ddc.dd_host_chunk_schedule(nout, pitch, tile, reach)
+        ntile = -(-nout // tile)
+        assert 1 <= len(col) <= 8 and len(col) == min(8, ntile)
+        assert til[-1] == ntile and np.all(np.diff(np.concatenate([[0], til])) > 0)
+        assert col[-1] == pitch and np.all(np.diff(col) >= 0)
+        for c in range(len(col)):
+            assert min(pitch, int(til[c]) * tile + reach) <= col[c]
