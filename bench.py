@@ -35,8 +35,36 @@ import synth  # noqa: E402
 METRIC = "DM-trial·samples/s"
 WORKLOAD = "lofar_f32"
 # ncu DRAM bytes (read + write) per de-dispersion launch, keyed by the
-# (tile configuration, raster group) the capture used
-PROFILED_TRAFFIC = {(5, 16): 25.63e9, (11, 16): 21.41e9}
+# (tile configuration, raster group) the capture used, with the digest of the
+# kernel's source files at capture time (kernel_source_digest): the figure is
+# reported only while the sources are unchanged.  Empty: the captures in
+# profiles/ (21.41 GB for config 11, 25.63 GB for config 5) predate edits to
+# those kernels.
+PROFILED_TRAFFIC = {}
+KERNEL_SOURCES = {3: ("dd_lane_impl.cuh", "dd_lane_c2.cu", "dd_device.cuh", "dd_fast_impl.cuh"),
+                  5: ("dd_share_impl.cuh", "dd_share.cu", "dd_lane_impl.cuh", "dd_device.cuh", "dd_fast_impl.cuh")}
+
+
+def kernel_source_digest(kernel_id: int) -> str:
+    """sha256 over the source files that define a de-dispersion kernel."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1107_2516_gb300", "csrc")
+    for f in KERNEL_SOURCES.get(kernel_id, ()):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel_id: int, tile):
+    """The recorded ncu traffic of this launch configuration, or None if there
+    is none or the kernel's sources changed since it was captured."""
+    if not tile:
+        return None
+    rec = PROFILED_TRAFFIC.get(tuple(tile[:2]))
+    if rec is None or rec[1] != kernel_source_digest(kernel_id):
+        return None
+    return rec[0]
 
 # tile configurations of dd_plan_set_tile: (kernel, samples per thread or lane,
 # DM trials per thread or warp, warps per block)
@@ -353,11 +381,9 @@ def run_ours(args, rank, world, local_rank):
     roof = {"bound": "alu", "kernel": f"dd kernel {kernel_id} (de-dispersion{tile_s})",
             "achieved": achieved, "peak": peak, "unit": "Gadd/s", "frac": achieved / peak,
             "peak_basis": f"{sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",
-            # dram__bytes_read.sum + dram__bytes_write.sum of one launch, from the ncu
-            # captures summarised in profiles/dedisp_kernel3_lofar_f32.md (config 5)
-            # and profiles/dedisp_kernel5_lofar_f32.md (config 11); only for the
-            # tile each was taken with (null otherwise)
-            "traffic": PROFILED_TRAFFIC.get(tuple(tile[:2])) if tile else None,
+            # dram__bytes_read.sum + dram__bytes_write.sum of one launch from an ncu
+            # capture of this tile with these kernel sources (null otherwise)
+            "traffic": profiled_traffic(kernel_id, tile),
             "traffic_unit": "bytes per launch",
             "kernel_ms": ker_ms}
     if kernel_id == 5:

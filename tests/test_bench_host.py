@@ -69,3 +69,15 @@ def test_pipeline_schedule_covers_every_tile(seed):
         assert col[-1] == pitch and np.all(np.diff(col) >= 0)
         for c in range(len(col)):
             assert min(pitch, int(til[c]) * tile + reach) <= col[c]
+
+
+def test_traffic_reported_only_for_unchanged_sources(monkeypatch):
+    # a recorded ncu traffic figure is reported while the kernel's sources
+    # still hash to the digest taken with it, and dropped once they change
+    dig = bench.kernel_source_digest(5)
+    assert len(dig) == 64 and dig != bench.kernel_source_digest(3)
+    monkeypatch.setattr(bench, "PROFILED_TRAFFIC", {(11, 16): (21.41e9, dig), (9, 16): (25.6e9, "0" * 64)})
+    assert bench.profiled_traffic(5, (11, 16, 16, 6)) == 21.41e9
+    assert bench.profiled_traffic(5, (9, 16, 16, 4)) is None
+    assert bench.profiled_traffic(5, (10, 16, 8, 4)) is None
+    assert bench.profiled_traffic(5, None) is None
