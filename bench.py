@@ -427,7 +427,9 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": e2e_value, "unit": METRIC,
                 "h2d_bytes_per_step": int(wl.nchans * wl.nsamp * 4),
                 "d2h_bytes_per_step": int(8 + 32 * min(total, 1 << 16) + 272)},
-        "gpu_launches": 3 * args.steps,
+        # per step: the de-dispersion kernel, finalize_kernel (statistics),
+        # the boxcar search kernel and cand_snr_kernel
+        "gpu_launches": 4 * args.steps,
         "clocks": clk,
         "roofline": roof,
     }
