@@ -70,8 +70,13 @@ typedef enum {
     DD_ERR_OVERFLOW = 4,  /* more candidates than the caller's capacity      */
     DD_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up              */
     DD_ERR_BUDGET = 6,    /* admission refused: the HBM budget is exhausted  */
-    DD_PRIMING = 7        /* server chunk accepted, no output yet: the beam's
+    DD_PRIMING = 7,       /* server chunk accepted, no output yet: the beam's
                              resident history holds < maxshift samples       */
+    DD_ERR_SEQ = 8,       /* server chunk refused: its seq repeats or precedes
+                             the beam's last accepted chunk (nothing queued) */
+    DD_SEQ_GAP = 9        /* server chunk accepted after a gap in seq: the
+                             beam's stream restarts at it (history zeroed,
+                             the beam primes again)                          */
 } dd_status;
 
 typedef struct dd_server dd_server;
@@ -352,9 +357,15 @@ DD_API int dd_server_create(int64_t hbm_budget_bytes, int32_t nworkers, int64_t 
 DD_API int dd_server_destroy(dd_server *server);
 
 /* Admit a beam (plan parameters as dd_plan_create, `chunk` new samples per
- * submission).  The beam's device memory (two history rings of
- * nchans x (maxshift + chunk) samples, the output, the plan) is reserved
- * against the budget: DD_ERR_BUDGET if it does not fit (nothing allocated). */
+ * submission).  The beam's device memory (one sample ring of nchans rows x
+ * about maxshift + K*chunk columns, K = 2 + floor(maxshift/chunk); the
+ * output; the plan) is reserved against the budget: DD_ERR_BUDGET if it does
+ * not fit (nothing allocated).  Each chunk is de-dispersed in place from the
+ * ring (its window's base moves by one chunk per submission); the last
+ * maxshift samples are moved to the ring's front once every K chunks.  The
+ * beam runs kernel 5 where its tables fit the plan, else the plan's default
+ * kernel; with dd_server_set_autotune on, the autotuner's choice timed on
+ * the beam's own buffers at admission (cached per plan shape). */
 DD_API int dd_server_add_beam(dd_server *server, int32_t nchans, double fch1_mhz, double foff_mhz,
                               double tsamp_s, const double *dm_list, int32_t ndm,
                               const int32_t *boxcar_widths, int32_t nwidths, double sigma_k,
@@ -378,7 +389,14 @@ DD_API int dd_server_set_boundary_search(dd_server *server, int32_t beam, int32_
 
 /* Queue one chunk: chunk_host holds nchans rows of `chunk` samples,
  * host_pitch elements apart (pinned or pageable).  It must stay valid and
- * unchanged until dd_server_poll reports the chunk.  Returns immediately. */
+ * unchanged until dd_server_poll reports the chunk.  Returns immediately.
+ * Sequence numbers: the beam's first chunk may carry any seq; each later one
+ * must carry the previous accepted seq + 1 (DD_OK).  A larger seq means
+ * chunks were lost: the chunk is queued, and the beam's stream restarts at it
+ * (its history is zeroed, no boxcar joins the two parts, and the next
+ * ceil(maxshift/chunk) chunks report DD_PRIMING): returns DD_SEQ_GAP.  A
+ * seq that repeats or precedes the last accepted one is refused with
+ * DD_ERR_SEQ and nothing is queued (the caller keeps ownership at once). */
 DD_API int dd_server_submit(dd_server *server, int32_t beam, const void *chunk_host, int64_t host_pitch,
                             int64_t seq);
 
@@ -398,8 +416,49 @@ DD_API int dd_server_candidates(dd_server *server, int32_t beam, int64_t seq, dd
 DD_API int dd_server_beam_info(dd_server *server, int32_t beam, int64_t *maxshift, int64_t *chunk,
                                int64_t *ndm, void **out_dev, int64_t *device_bytes);
 
+/* Beams admitted from now on: on = 1 runs dd_plan_autotune on each beam's
+ * own buffers at admission (the choice is cached process-wide per plan
+ * shape, so a beam shaped like an earlier one is not timed again); on = 0
+ * (the default) takes kernel 5 where available without timing. */
+DD_API int dd_server_set_autotune(dd_server *server, int32_t on);
+
+/* The kernel (dd_plan_get_kernel) and tile configuration (dd_plan_get_tile;
+ * -1 for kernel 1) a beam runs; either pointer may be NULL. */
+DD_API int dd_server_beam_kernel(dd_server *server, int32_t beam, int32_t *kernel, int32_t *config);
+
+/* The host-side schedule the server follows for one beam, computed alone
+ * (host code, no device work), so that it can be checked without a GPU.
+ * For n submissions with sequence numbers seq[i] on a beam of maxshift M
+ * and `chunk` samples per submission: *span = the ring's columns in use
+ * (M + K*chunk); submit_status[i] = DD_OK, DD_SEQ_GAP or DD_ERR_SEQ as
+ * dd_server_submit returns it; restart[i] = 1 if the stream restarts at i;
+ * move_src[i] = the column whose M samples move to columns [0, M) before
+ * chunk i is written (-1: no move); write_col[i] = the column of chunk i's
+ * first sample; window_col[i] = the column of its de-dispersion window's
+ * first sample (window = [window_col, window_col + M + chunk)); priming[i] =
+ * 1 if it reports DD_PRIMING.  Refused submissions get -1 columns and
+ * priming 0.  All arrays hold n entries (caller-owned).  DD_ERR_ARG for
+ * M < 0, chunk < 1 or NULL arrays. */
+DD_API int dd_server_ring_schedule(int64_t maxshift, int64_t chunk, int32_t n, const int64_t *seq,
+                                   int64_t *span, int32_t *submit_status, int32_t *restart,
+                                   int64_t *move_src, int64_t *write_col, int64_t *window_col,
+                                   int32_t *priming);
+
 /* Bytes reserved by admitted beams and the budget. */
 DD_API int dd_server_memory(dd_server *server, int64_t *used, int64_t *budget);
+
+/* Self-test of the bounded device waits (no counterpart in the paper: the
+ * failure path of the staged kernels).  Every kernel that stages its input
+ * with TMA copies waits on an mbarrier with a time limit; if a copy never
+ * completes it records DD_ERR_TIMEOUT and returns instead of hanging, and the
+ * host reports that status.  This runs one block that arms an mbarrier for 16
+ * bytes and waits with that same bounded wait, its limit shortened to
+ * limit_ns (1 .. 2e9): with issue_copy = 0 no copy is issued, nothing is left
+ * in flight, and the wait runs out (returns DD_ERR_TIMEOUT, *device_status =
+ * DD_ERR_TIMEOUT); with issue_copy = 1 the 16-byte copy completes it
+ * (DD_OK, *device_status = 0).  Synchronous on the legacy default stream;
+ * allocates and frees 32 device bytes.  DD_ERR_ARG for a limit out of range. */
+DD_API int dd_wait_selftest(int64_t limit_ns, int32_t issue_copy, int32_t *device_status);
 
 /* Allocation-free statistics (no counterpart in the paper).  For callers that
  * cannot call cudaMalloc — e.g. a real-time pipeline whose device memory is
@@ -412,7 +471,10 @@ DD_API int dd_server_memory(dd_server *server, int64_t *used, int64_t *budget);
  * every GPU loading the library holds until exit, which limits n to
  * 1 <= n <= 268435456 (2^28); larger n returns DD_ERR_ARG without launching.
  * The first call on each device looks up that array's device address (with
- * the device current); make that first call before any stream capture.
+ * the device current); make that first call before any stream capture.  The
+ * address is kept for the life of the process: do not use this call on a
+ * device after cudaDeviceReset (the module is reloaded and the kept address
+ * no longer names the array).
  * Every call on a device shares the array, so calls whose kernels overlap on
  * the GPU (different streams, no ordering between them) race and may return
  * wrong values; calls ordered on one stream are safe. */

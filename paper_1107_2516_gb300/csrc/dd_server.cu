@@ -7,7 +7,19 @@
 // that arrive while others are on the GPU start immediately and overlap on the
 // device (continuous batching).  Beams are admitted against a device-memory
 // budget.
+//
+// Each beam's samples live in one device ring of nchans rows x `span` =
+// maxshift + K*chunk columns.  Chunk k is written behind the previous one and
+// de-dispersed in place from the window [write - maxshift, write + chunk):
+// the window's base moves by one chunk per submission, and only when the next
+// chunk would run past `span` are the last maxshift samples moved to the front
+// (once per K chunks; K = 2 + floor(maxshift / chunk) keeps the move's source
+// and destination disjoint).  Sequence numbers are checked on submission: a
+// chunk that repeats or precedes the last accepted one is refused, and a chunk
+// after a gap restarts the beam's stream (zeroed history, priming again)
+// instead of joining unrelated samples.
 #include "dd_internal.h"
+#include "dd_ring.h"
 
 #include <algorithm>
 #include <chrono>
@@ -33,6 +45,7 @@ struct Pending {
     const void *host;
     int64_t host_pitch;
     double t_submit;
+    bool restart;        // first chunk after a gap in seq: the stream starts over
 };
 
 struct ServerBeam {
@@ -40,8 +53,9 @@ struct ServerBeam {
     dd_plan *plan = nullptr;
     int64_t chunk = 0, maxshift = 0, nin = 0, pitch = 0;
     size_t eb = 1;
-    void *ring[2] = {nullptr, nullptr};
-    int cur = 0;
+    void *ring = nullptr;     // [nchans][pitch] samples; the window base moves (dd::Ring)
+    dd::Ring r;
+    dd::SeqCheck sq;
     void *out = nullptr;
     // boundary search (optional): the previous chunk's last L outputs per row
     bool carry = false, tail_valid = false;
@@ -68,6 +82,7 @@ struct dd_server {
     std::deque<dd_chunk_result> done;
     std::map<std::pair<int, int64_t>, std::vector<dd_candidate>> cands;
     bool stop = false;
+    bool autotune = false;
 };
 
 namespace dd {
@@ -75,8 +90,7 @@ namespace dd {
 static void free_beam(ServerBeam *b)
 {
     if (b->plan) dd_plan_destroy(b->plan);
-    for (void *r : b->ring)
-        if (r) cudaFree(r);
+    if (b->ring) cudaFree(b->ring);
     if (b->out) cudaFree(b->out);
     if (b->tail) cudaFree(b->tail);
     delete b;
@@ -102,26 +116,31 @@ static void process(dd_server *S, ServerBeam *b, const Pending &pc, cudaStream_t
     r.t_submit = pc.t_submit;
     r.t_start = now_s();
     r.status = DD_OK;
-    const int nxt = 1 - b->cur;
     const size_t rowb = (size_t)b->pitch * b->eb;
-    // history: the last maxshift samples of the previous ring -> front of the next ring
+    const size_t hist = (size_t)b->maxshift * b->eb;
+    const size_t nch = (size_t)b->plan->nchans;
+    char *ring = static_cast<char *>(b->ring);
+    const Ring::Step st = b->r.next(pc.restart);
+    if (st.zero_history) b->tail_valid = false;      // no boundary window joins the two streams
     cudaError_t e = cudaSuccess;
-    if (b->maxshift > 0)
-        e = cudaMemcpy2DAsync(b->ring[nxt], rowb, (const char *)b->ring[b->cur] + (size_t)b->chunk * b->eb, rowb,
-                              (size_t)b->maxshift * b->eb, (size_t)b->plan->nchans, cudaMemcpyDeviceToDevice, s);
-    // new samples behind it
+    if (st.zero_history && hist)
+        e = cudaMemset2DAsync(ring, rowb, 0, hist, nch, s);
+    // the last maxshift samples to the front (once per K chunks)
+    if (e == cudaSuccess && st.move_src >= 0 && hist)
+        e = cudaMemcpy2DAsync(ring, rowb, ring + (size_t)st.move_src * b->eb, rowb, hist, nch,
+                              cudaMemcpyDeviceToDevice, s);
+    // the new samples behind the history
     if (e == cudaSuccess)
-        e = cudaMemcpy2DAsync((char *)b->ring[nxt] + (size_t)b->maxshift * b->eb, rowb, pc.host,
-                              (size_t)pc.host_pitch * b->eb, (size_t)b->chunk * b->eb, (size_t)b->plan->nchans,
-                              cudaMemcpyHostToDevice, s);
+        e = cudaMemcpy2DAsync(ring + (size_t)st.write_col * b->eb, rowb, pc.host, (size_t)pc.host_pitch * b->eb,
+                              (size_t)b->chunk * b->eb, nch, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
         r.status = cuda_fail(e, "server copies");
-    } else if (b->processed * b->chunk < b->maxshift) {
+    } else if (st.priming) {
         // the resident history does not yet hold maxshift real samples
         e = cudaStreamSynchronize(s);
         r.status = e == cudaSuccess ? DD_PRIMING : cuda_fail(e, "server sync");
     } else {
-        int rc = dd_execute(b->plan, b->ring[nxt], b->pitch, b->out, s);
+        int rc = dd_execute(b->plan, ring + (size_t)st.window_col * b->eb, b->pitch, b->out, s);
         int64_t n = 0;
         found.resize((size_t)S->cand_cap);
         if (rc == DD_OK) rc = dd_search(b->plan, b->out, found.data(), S->cand_cap, &n, s);
@@ -170,7 +189,6 @@ static void process(dd_server *S, ServerBeam *b, const Pending &pc, cudaStream_t
         r.status = rc;
         r.n_candidates = n;
     }
-    b->cur = nxt;
     b->processed++;
     r.t_done = now_s();
 }
@@ -262,28 +280,49 @@ int dd_server_add_beam(dd_server *S, int32_t nchans, double fch1, double foff, d
     const size_t eb = in_elem_bytes((dd_dtype)dtype);
     const int64_t nin = M + chunk;
     const int64_t al = 16 / (int64_t)eb;
-    const int64_t pitch = (nin + al - 1) / al * al;
-    // device bytes: two rings, the output, and the plan's tables (delay-table sized estimate)
+    // ring pitch: the span, aligned, plus one aligned unit (the tiled kernels
+    // stage an input row up to nsamp_in rounded up to that unit)
+    const int64_t pitch = (Ring::span_of(M, chunk) + al - 1) / al * al + al;
+    // device bytes: the ring, the output, and the plan's tables (delay-table sized estimate)
     const size_t ring_b = (size_t)nchans * (size_t)pitch * eb;
     const size_t out_b = (size_t)ndm * (size_t)chunk * 4;
     const size_t tab_b = (size_t)ndm * (size_t)nchans * 4 * 8;
-    const size_t need = 2 * ring_b + out_b + tab_b;
+    const size_t need = ring_b + out_b + tab_b;
+    bool tune;
     {
         std::lock_guard<std::mutex> g(S->mu);
         if (S->used + (int64_t)need > S->budget)
             return set_error(DD_ERR_BUDGET, "admission refused: beam needs %zu bytes, %lld of %lld in use",
                              need, (long long)S->used, (long long)S->budget);
         S->used += (int64_t)need;    // reserve before allocating
+        tune = S->autotune;
     }
     ServerBeam *b = new ServerBeam();
     b->chunk = chunk; b->maxshift = M; b->nin = nin; b->pitch = pitch; b->eb = eb; b->bytes = need;
+    b->r.init(M, chunk);
     rc = dd_plan_create(nchans, fch1, foff, tsamp, dm_list, ndm, widths, nwidths, sigma, dtype, nin, &b->plan);
     cudaError_t e = cudaSuccess;
-    if (rc == DD_OK) e = cudaMalloc(&b->ring[0], ring_b);
-    if (rc == DD_OK && e == cudaSuccess) e = cudaMalloc(&b->ring[1], ring_b);
+    if (rc == DD_OK) e = cudaMalloc(&b->ring, ring_b);
     if (rc == DD_OK && e == cudaSuccess) e = cudaMalloc(&b->out, out_b);
-    if (rc == DD_OK && e == cudaSuccess) e = cudaMemset(b->ring[0], 0, ring_b);
+    if (rc == DD_OK && e == cudaSuccess) e = cudaMemset(b->ring, 0, ring_b);
     if (rc == DD_OK && e != cudaSuccess) rc = cuda_fail(e, "beam buffers");
+    if (rc == DD_OK) {
+        // kernel 5 (shared subband partial sums) where its tables fit this
+        // beam, else the plan's default; or, on request, the autotuner's pick
+        // timed on the beam's own (zeroed) buffers, cached per plan shape
+        if (tune) {
+            cudaStream_t ts = nullptr;
+            e = cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking);
+            if (e == cudaSuccess) {
+                rc = dd_plan_autotune(b->plan, b->ring, pitch, b->out, ts);
+                cudaStreamDestroy(ts);
+            } else {
+                rc = cuda_fail(e, "admission stream");
+            }
+        } else if (dd_plan_set_kernel(b->plan, 5) != DD_OK) {
+            set_error(DD_OK, "%s", "");
+        }
+    }
     std::lock_guard<std::mutex> g(S->mu);
     if (rc != DD_OK) {
         S->used -= (int64_t)need;
@@ -344,9 +383,19 @@ int dd_server_submit(dd_server *S, int32_t beam, const void *chunk_host, int64_t
     std::lock_guard<std::mutex> g(S->mu);
     auto it = S->beams.find(beam);
     if (it == S->beams.end() || it->second->removed) return set_error(DD_ERR_ARG, "no beam %d", beam);
-    if (host_pitch < it->second->chunk) return set_error(DD_ERR_ARG, "host_pitch < chunk");
-    it->second->queue.push_back(Pending{seq, chunk_host, host_pitch, t});
+    ServerBeam *b = it->second;
+    if (host_pitch < b->chunk) return set_error(DD_ERR_ARG, "host_pitch < chunk");
+    bool restart = false;
+    const int64_t expect = b->sq.next;
+    const int rc = b->sq.admit(seq, &restart);
+    if (rc == DD_ERR_SEQ)
+        return set_error(DD_ERR_SEQ, "beam %d: chunk seq %lld refused (next expected %lld): repeated or late",
+                         beam, (long long)seq, (long long)expect);
+    b->queue.push_back(Pending{seq, chunk_host, host_pitch, t, restart});
     S->cv_work.notify_one();
+    if (rc == DD_SEQ_GAP)
+        return set_error(DD_SEQ_GAP, "beam %d: chunks %lld..%lld missing; the stream restarts at %lld",
+                         beam, (long long)expect, (long long)seq - 1, (long long)seq);
     return DD_OK;
 }
 
@@ -392,6 +441,58 @@ int dd_server_beam_info(dd_server *S, int32_t beam, int64_t *maxshift, int64_t *
     if (ndm) *ndm = b->plan->ndm;
     if (out_dev) *out_dev = b->out;
     if (device_bytes) *device_bytes = (int64_t)b->bytes;
+    return DD_OK;
+}
+
+int dd_server_set_autotune(dd_server *S, int32_t on)
+{
+    if (!S) return set_error(DD_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> g(S->mu);
+    S->autotune = on != 0;
+    return DD_OK;
+}
+
+int dd_server_beam_kernel(dd_server *S, int32_t beam, int32_t *kernel, int32_t *config)
+{
+    if (!S) return set_error(DD_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->beams.find(beam);
+    if (it == S->beams.end()) return set_error(DD_ERR_ARG, "no beam %d", beam);
+    int rc = DD_OK;
+    if (kernel) rc = dd_plan_get_kernel(it->second->plan, kernel);
+    if (rc == DD_OK && config) {
+        int32_t grp = 0, ti = 0, nw = 0;
+        if (dd_plan_get_tile(it->second->plan, config, &grp, &ti, &nw) != DD_OK) *config = -1;
+    }
+    return rc;
+}
+
+int dd_server_ring_schedule(int64_t maxshift, int64_t chunk, int32_t n, const int64_t *seq, int64_t *span,
+                            int32_t *submit_status, int32_t *restart, int64_t *move_src, int64_t *write_col,
+                            int64_t *window_col, int32_t *priming)
+{
+    if (maxshift < 0 || chunk < 1 || n < 0 || (n > 0 && (!seq || !submit_status || !restart || !move_src ||
+                                                         !write_col || !window_col || !priming)))
+        return set_error(DD_ERR_ARG, "bad arguments");
+    SeqCheck sq;
+    Ring r;
+    r.init(maxshift, chunk);
+    if (span) *span = r.span;
+    for (int32_t i = 0; i < n; ++i) {
+        bool rs = false;
+        submit_status[i] = sq.admit(seq[i], &rs);
+        restart[i] = rs ? 1 : 0;
+        if (submit_status[i] == DD_ERR_SEQ) {
+            move_src[i] = write_col[i] = window_col[i] = -1;
+            priming[i] = 0;
+            continue;
+        }
+        const Ring::Step st = r.next(rs);
+        move_src[i] = st.move_src;
+        write_col[i] = st.write_col;
+        window_col[i] = st.window_col;
+        priming[i] = st.priming ? 1 : 0;
+    }
     return DD_OK;
 }
 

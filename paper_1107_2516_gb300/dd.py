@@ -40,9 +40,10 @@ EXPORTS = ("dd_plan_create", "dd_plan_destroy", "dd_plan_info", "dd_execute", "d
            "dd_survey_plan_create", "dd_survey_plan_destroy", "dd_survey_pass_info", "dd_survey_execute",
            "dd_survey_search", "dd_survey_last_stats", "dd_channelise",
            "dd_plan_set_search_stats", "dd_last_row_stats", "dd_cluster_candidates",
-           "dd_server_set_boundary_search")
+           "dd_server_set_boundary_search", "dd_server_set_autotune", "dd_server_beam_kernel",
+           "dd_server_ring_schedule", "dd_wait_selftest")
 
-DD_PRIMING = 7
+DD_PRIMING, DD_ERR_SEQ, DD_SEQ_GAP = 7, 8, 9
 
 CLUSTER_DTYPE = np.dtype([("dm_idx", np.int32), ("width_idx", np.int32), ("t", np.int64),
                           ("snr", np.float32), ("n_members", np.int32), ("dm_lo", np.int32),
@@ -138,6 +139,10 @@ def load(path: Optional[str] = None):
             "dd_plan_set_search_stats": (C.c_int, [vp, i32]),
             "dd_cluster_candidates": (C.c_int, [vp, i64, i32, i64, vp, i64, P64, vp]),
             "dd_server_set_boundary_search": (C.c_int, [vp, i32, i32]),
+            "dd_server_set_autotune": (C.c_int, [vp, i32]),
+            "dd_wait_selftest": (C.c_int, [i64, i32, C.POINTER(i32)]),
+            "dd_server_beam_kernel": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
+            "dd_server_ring_schedule": (C.c_int, [i64, i64, i32, vp, P64, vp, vp, vp, vp, vp, vp]),
             "dd_last_row_stats": (C.c_int, [vp, vp, vp]),
             "dd_last_error": (C.c_char_p, []),
             "dd_version": (C.c_char_p, []),
@@ -348,6 +353,28 @@ def dd_host_chunk_schedule(nsamp_out: int, pitch: int, tile: int, reach: int):
     return col[:n.value].copy(), til[:n.value].copy()
 
 
+def dd_wait_selftest(limit_ns: int, issue_copy: bool):
+    """Bounded-wait self-test: (return status, device status); never raises."""
+    st = C.c_int32(-1)
+    rc = load().dd_wait_selftest(int(limit_ns), 1 if issue_copy else 0, C.byref(st))
+    return int(rc), int(st.value)
+
+
+def dd_server_ring_schedule(maxshift: int, chunk: int, seqs):
+    """The server's host-side schedule for one beam (no device work): dict of
+    span and, per submission, status, restart, move_src, write_col, window_col,
+    priming (numpy arrays)."""
+    sq = np.ascontiguousarray(np.asarray(seqs, dtype=np.int64))
+    n = sq.size
+    st, rs, pr = (np.zeros(max(n, 1), np.int32) for _ in range(3))
+    mv, wc, wn = (np.zeros(max(n, 1), np.int64) for _ in range(3))
+    span = C.c_int64()
+    _check(load().dd_server_ring_schedule(int(maxshift), int(chunk), int(n), _ptr(sq), C.byref(span), _ptr(st),
+                                          _ptr(rs), _ptr(mv), _ptr(wc), _ptr(wn), _ptr(pr)))
+    return {"span": int(span.value), "status": st[:n], "restart": rs[:n], "move_src": mv[:n],
+            "write_col": wc[:n], "window_col": wn[:n], "priming": pr[:n]}
+
+
 def dd_share_tables(delays: np.ndarray, foff: float, dtype: int, config: int):
     """Kernel 5's tables (host only) for a delay table [ndm][nchans]: None if the
     shape cannot run it, else dict(rec [blocks][subbands][kLen], base
@@ -401,11 +428,24 @@ class Server:
         """Also search boxcars crossing from the previous chunk (reported with t < 0)."""
         _check(load().dd_server_set_boundary_search(self.handle, int(beam), 1 if on else 0))
 
-    def submit(self, beam: int, chunk_host, host_pitch: int, seq: int) -> None:
-        """chunk_host must stay alive and unchanged until poll() reports (beam, seq)."""
+    def submit(self, beam: int, chunk_host, host_pitch: int, seq: int) -> int:
+        """chunk_host must stay alive and unchanged until poll() reports (beam, seq).
+        Returns DD_OK, or DD_SEQ_GAP when the beam's stream restarts at this
+        chunk; raises DDError(DD_ERR_SEQ) for a repeated or late seq (nothing queued)."""
+        rc = load().dd_server_submit(self.handle, int(beam), _ptr(chunk_host), int(host_pitch), int(seq))
+        _check(rc, allow=(DD_SEQ_GAP,))
         self._keep[(int(beam), int(seq))] = chunk_host
-        _check(load().dd_server_submit(self.handle, int(beam), _ptr(chunk_host), int(host_pitch),
-                                       int(seq)))
+        return rc
+
+    def set_autotune(self, on: bool = True) -> None:
+        """Autotune beams admitted from now on (on their own buffers, cached per plan shape)."""
+        _check(load().dd_server_set_autotune(self.handle, 1 if on else 0))
+
+    def beam_kernel(self, beam: int):
+        """(kernel, tile configuration) the beam runs."""
+        k, c = C.c_int32(), C.c_int32()
+        _check(load().dd_server_beam_kernel(self.handle, int(beam), C.byref(k), C.byref(c)))
+        return int(k.value), int(c.value)
 
     def poll(self, max_results: int = 256, wait_ms: int = 0) -> np.ndarray:
         res = np.zeros(max_results, dtype=CHUNK_RESULT_DTYPE)
