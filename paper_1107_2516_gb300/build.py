@@ -16,7 +16,7 @@ LIB = os.path.join(HERE, "libdd.so")
 SOURCES = ["dd_api.cu", "dd_kernels.cu", "dd_fast.cu", "dd_fast_t36w8.cu", "dd_fast_t20w12.cu",
            "dd_fast_t28w8.cu", "dd_lane_c0.cu", "dd_lane_c1.cu", "dd_lane_c2.cu", "dd_lane_c3.cu", "dd_tmem_c0.cu",
            "dd_tmem_c1.cu", "dd_share.cu", "dd_noalloc.cu", "dd_subband.cu", "dd_frontend.cu", "dd_cluster.cu",
-           "dd_server.cu"]
+           "dd_server.cu", "dd_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -89,13 +89,16 @@ __device__ __forceinline__ uint64_t gtimer()
     return t;
 }
 
-// Bounded wait: gives up after ~2 s, records DD_ERR_TIMEOUT, returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err)
+// Bounded wait: gives up after limit_ns (default ~2 s), records
+// DD_ERR_TIMEOUT, returns false.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err,
+                                          uint64_t limit_ns = kWaitLimitNs)
 {
     if (mbar_test(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (!mbar_test(bar, parity)) {
-        if (gtimer() - t0 > 2000000000ull) {
+        if (gtimer() - t0 > limit_ns) {
             atomicExch(err, DD_ERR_TIMEOUT);
             return false;
         }
