@@ -331,3 +331,38 @@ def test_process_host_pipelined(dtype, kernel, tile):
         assert abs(mu1 - mu2) <= 1e-12 * max(1.0, abs(mu2)) and abs(sg1 - sg2) <= 1e-12 * sg2
         assert np.max(np.abs(c1["snr"].astype(np.float64) - c2["snr"])) <= 1e-4
     plan.close()
+
+
+def test_measured_precision_errors(capsys):
+    """The precision variants' measured error against the FP64 oracle on the
+    config-1 shape (128 channels, 64 DM trials, 8192 samples, noise + the
+    amplitude-5 pulse): float32 input, the same data rounded to FP16 (oracle
+    on the rounded values) and quantised to uint8 (exact integers), for every
+    kernel that runs this plan.  Bound: 1e-5 * nchans = 1.28e-3."""
+    wl = SMALL
+    d_o, m_o = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
+    nout = wl.nsamp - m_o
+    rows = []
+    for dtype in ("f32", "f16", "u8"):
+        arr, _ = make_input(wl.nchans, wl.nsamp, wl.fch1, wl.foff, wl.tsamp, wl.seed, small_pulse(), dtype)
+        ora = oracle.dedisperse(arr, d_o, nout)
+        for kernel in (1, 2, 3, 4):
+            plan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, wl.sigma,
+                           DTYPES[dtype], wl.nsamp)
+            plan.set_kernel(kernel)
+            out_dev = torch.empty(wl.ndm * nout, dtype=torch.int32 if dtype == "u8" else torch.float32,
+                                  device="cuda")
+            plan.execute(to_device(arr), arr.shape[1], out_dev)
+            torch.cuda.synchronize()
+            out = out_dev.cpu().numpy().reshape(wl.ndm, nout).astype(np.float64)
+            err = float(np.max(np.abs(out - ora)))
+            rows.append((dtype, kernel, err, float(np.sqrt(np.mean((out - ora) ** 2)))))
+            plan.close()
+    msg = "; ".join(f"{dt} kernel {k}: max|err| {e:.3g} rms {r:.3g}" for dt, k, e, r in rows)
+    with capsys.disabled():
+        print(f"\nprecision (config 1/3 shape, bound {fp_tol(wl.nchans):.3g}): {msg}")
+    for dt, k, e, _ in rows:
+        if dt == "u8":
+            assert e == 0.0, msg
+        else:
+            assert e <= fp_tol(wl.nchans), msg
