@@ -14,9 +14,11 @@
 // its table record):
 //   stage 1: the block forms every pattern's partial sum over the samples
 //            its trials need (P, double-buffered in shared memory).  The
-//            patterns' sums are laid end to end in one index space e < E and
-//            the block's threads stride through it together, so every thread
-//            gets the same number of sums whatever the patterns' lengths;
+//            patterns' sums are laid end to end in one index space e < E,
+//            cut into rows of 32 (each row inside one pattern), and each warp
+//            sums a contiguous run of rows, four rows per step: the pattern's
+//            fields are uniform in the warp and reloaded only where a pattern
+//            ends, and every warp gets the same number of rows;
 //   stage 2: each warp adds, for its trials, P_pat[t + offset] (one
 //            conflict-free shared word per add, as kernel 3).
 // One __syncthreads per subband: stage 1 of subband s+1 writes the other P
@@ -65,34 +67,58 @@ struct ShareLaunch {
     size_t smem;
 };
 
-// Stage 1 of one subband: P[e] for e < E (the patterns' sums end to end),
-// threads t, t + nt, t + 2 nt, ...  Patterns are at least nt long, so a
-// thread moves on by at most one pattern per step.
-template <typename Tin, typename R, int CS>
-__device__ __forceinline__ void share_stage1(const int32_t *rec, const Tin *srow, float *Pb, int t, int nt)
+// Stage 1 of one subband: P[e] for e < E (the patterns' sums end to end).
+// Each pattern's sums form rows of 32 consecutive e (the last one partial);
+// warp w takes the contiguous rows [w R / NW, (w+1) R / NW) of all R rows, so
+// a row's pattern (its fields) is uniform in the warp and changes only at
+// pattern ends, and lane l sums element row_start + l of each of its rows,
+// four rows at a time.
+template <typename Tin, typename R, int CS, int NW, int NPMAX>
+__device__ __forceinline__ void share_stage1(const int32_t *rec, const Tin *srow, float *Pb, int warp, int lane)
 {
+    static_assert(NPMAX <= 32, "one pattern per lane");
     const int E = rec[R::kE];
-    const int32_t *pr = rec + R::kPat;
-    int f[R::kPatLen];
+    // lane p < npat: pattern p's end, start, rows; unused slots hold end 0
+    int end_p = lane < NPMAX ? rec[R::kPat + lane * R::kPatLen] : 0;
+    const int npat = __ffs(__ballot_sync(~0u, lane < NPMAX && end_p == E));
+    int start_p = __shfl_up_sync(~0u, end_p, 1);
+    if (lane == 0) start_p = 0;
+    const int rows_p = lane < npat ? (end_p - start_p + 31) >> 5 : 0;
+    int incl = rows_p;
 #pragma unroll
-    for (int v = 0; v < R::kPatLen; v += 4) {
-        const int4 x = *reinterpret_cast<const int4 *>(pr + v);
-        f[v] = x.x; f[v + 1] = x.y; f[v + 2] = x.z; f[v + 3] = x.w;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(~0u, incl, o);
+        if (lane >= o) incl += v;
     }
-#pragma unroll 2
-    for (int e = t; e < E; e += nt) {
-        while (e >= f[0]) {
-            pr += R::kPatLen;
+    const int rtot = __shfl_sync(~0u, incl, 31);
+    const int r1 = (warp + 1) * rtot / NW;
+    int r = warp * rtot / NW;
+    int p = __ffs(__ballot_sync(~0u, incl > r)) - 1;
+    while (r < r1) {
+        const int pincl = __shfl_sync(~0u, incl, p), pst = __shfl_sync(~0u, start_p, p);
+        const int pend = __shfl_sync(~0u, end_p, p), pexcl = pincl - __shfl_sync(~0u, rows_p, p);
+        const int32_t *pr = rec + R::kPat + p * R::kPatLen;
+        int b[R::kPatLen];
 #pragma unroll
-            for (int v = 0; v < R::kPatLen; v += 4) {
-                const int4 x = *reinterpret_cast<const int4 *>(pr + v);
-                f[v] = x.x; f[v + 1] = x.y; f[v + 2] = x.z; f[v + 3] = x.w;
+        for (int v = 0; v < R::kPatLen; v += 4) {
+            const int4 x = *reinterpret_cast<const int4 *>(pr + v);
+            b[v] = x.x; b[v + 1] = x.y; b[v + 2] = x.z; b[v + 3] = x.w;
+        }
+        const int rend = min(r1, pincl);
+        for (; r < rend; r += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = pst + ((r + u - pexcl) << 5) + lane;
+                if (r + u < rend && e < pend) {
+                    float v = lane_ld<Tin>(srow + b[1] + e);
+#pragma unroll
+                    for (int c = 1; c < CS; ++c) v += lane_ld<Tin>(srow + b[1 + c] + e);
+                    Pb[e] = v;
+                }
             }
         }
-        float v = lane_ld<Tin>(srow + f[1] + e);
-#pragma unroll
-        for (int c = 1; c < CS; ++c) v += lane_ld<Tin>(srow + f[1 + c] + e);
-        Pb[e] = v;
+        r = rend;
+        ++p;
     }
 }
 
@@ -242,7 +268,7 @@ __device__ __forceinline__ bool share_tile(const ShareLaunch &a, int blk, int64_
         const Tin *srow = rows + (size_t)buf * stage_elems;
         float *Pb = P + (size_t)(s & 1) * a.pmax;
         // stage 1: every pattern's partial sum over the samples its trials need
-        share_stage1<Tin, R, CS>(rec, srow, Pb, tid, kT);
+        share_stage1<Tin, R, CS, NW, NPMAX>(rec, srow, Pb, warp, lane);
         // this warp's trials: index of their t = t0 term in P
 #pragma unroll
         for (int j = 0; j < DR; j += 4) {

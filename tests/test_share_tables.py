@@ -114,3 +114,58 @@ def test_kernel5_tables_bad_config():
     d = np.zeros((4, 8), np.int32)
     with pytest.raises(dd.DDError):
         ddc.dd_share_tables(d, -1.0, dd.DD_F32, 5)
+
+
+def _stage1_rows(rec_row, db, nw):
+    """Kernel 5's stage-1 work split, restated: the patterns' sums (index space
+    e < E) cut into rows of 32 inside each pattern; warp w of nw takes rows
+    [w R / nw, (w+1) R / nw) and lane l element row_start + l of each.  Returns
+    (how often each e is summed, every e's pattern matches its row's)."""
+    E = int(rec_row[db])
+    ends = rec_row[db + 4:].reshape(-1, 8)[:, 0].astype(np.int64)
+    npat = int(np.nonzero(ends == E)[0][0]) + 1
+    starts = np.concatenate([[0], ends[:npat - 1]])
+    rows = (ends[:npat] - starts + 31) // 32
+    incl = np.cumsum(rows)
+    excl = incl - rows
+    R = int(incl[-1])
+    cover = np.zeros(E, np.int64)
+    for w in range(nw):
+        r0, r1 = w * R // nw, (w + 1) * R // nw
+        for r in range(r0, r1):
+            p = int(np.searchsorted(incl, r, side="right"))
+            e = starts[p] + 32 * (r - excl[p]) + np.arange(32)
+            e = e[e < ends[p]]
+            assert e.size and e.min() >= starts[p]
+            cover[e] += 1
+    return cover
+
+
+@pytest.mark.parametrize("config", [9, 10, 11])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_stage1_rows_cover_every_sum_once(case, config):
+    nch, fch1, foff, ts, dms, nsamp, dt = CASES[case]
+    d, _ = oracle.delays(nch, fch1, foff, ts, dms)
+    t = ddc.dd_share_tables(np.asarray(d), foff, dd.DD_U8 if dt == "u8" else dd.DD_F32, config)
+    if t is None:
+        pytest.skip("shape unavailable for this plan")
+    _, db = SHAPES[config]
+    nw = {9: 4, 10: 4, 11: 6}[config]
+    rec = t["rec"]
+    for b in range(rec.shape[0]):
+        for s in range(rec.shape[1]):
+            assert np.all(_stage1_rows(rec[b, s], db, nw) == 1), (b, s)
+
+
+def test_stage1_rows_cover_every_sum_once_lofar():
+    # the benchmark plan's tables (every block, every 16th subband), configs 9 and 11
+    wl = synth.workload("lofar_f32")
+    d, _ = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
+    for config, nw in ((9, 4), (11, 6)):
+        t = ddc.dd_share_tables(np.asarray(d), wl.foff, dd.DD_F32, config)
+        assert t is not None
+        _, db = SHAPES[config]
+        rec = t["rec"]
+        for b in range(rec.shape[0]):
+            for s in range(0, rec.shape[1], 16):
+                assert np.all(_stage1_rows(rec[b, s], db, nw) == 1), (config, b, s)
