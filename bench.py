@@ -433,6 +433,26 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
         "roofline": roof,
     }
+    if world == 1 and not args.no_batch_serve:
+        # the batched and the serving forms on the same GPU, beside the plain
+        # single-beam line: 24 uneven beams in one CUDA graph, and 64 streaming
+        # beams under real-time arrival (latency) and a burst (capacity)
+        del host, pinned
+        torch.cuda.empty_cache()
+        bt = batch_measure(torch, dd, steps=3, warmup=1)
+        sv = serve_measure(torch, dd, args.serve_window, args.speed, args.workers, args.budget_frac, args.burst)
+        line["batched"] = bt
+        line["serving"] = sv
+        line["plain_vs_batched_serving"] = {
+            "plain_single_beam_f32": {"value": value, "latency_s": ms_per_step / 1e3,
+                                      "buffer_duration_s": nout * wl.tsamp},
+            "batched_24_beams": {"value": bt["value"], "latency_s": bt["ms_per_step"] / 1e3},
+            "serving_64_beams": {"capacity_value": sv["value"],
+                                 "realtime_p50_s": sv["realtime"]["latency_s"]["p50"],
+                                 "realtime_p99_s": sv["realtime"]["latency_s"]["p99"],
+                                 "realtime_rtf_min": sv["realtime"]["real_time_factor"]["min"]},
+            "unit": METRIC,
+        }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sample()
     print(json.dumps(line), flush=True)
@@ -448,24 +468,21 @@ def _device_beam_input(torch, b, pitch, seed):
     return x
 
 
-def run_batch(args):
-    """24 uneven beams (float32/uint8 mix, 256-4096 channels, 2^16-2^20 samples,
-    500-4000 DM trials): one persistent launch per batch, replayed from a CUDA
-    graph, against the same beams run one after another through dd_execute +
-    dd_search.  Prints one JSON line (mode "batch")."""
-    import torch
-    import paper_1107_2516_gb300 as dd
-    from paper_1107_2516_gb300 import build as ddbuild
-
-    ddbuild.build()
-    dd.load()
-
+def batch_measure(torch, dd, steps, warmup, full_autotune=False, sequential=True):
+    """The 24-beam batched workload (float32/uint8 mix, 256-4096 channels,
+    2^16-2^20 samples, 500-4000 DM trials): the whole batch (every beam's
+    de-dispersion + search) replayed from one CUDA graph, against the same
+    beams run one after another through dd_execute + dd_search.  The launch
+    configuration is the batch autotuner's choice (full_autotune), or else the
+    faster of the two launch modes of the default mixed configuration (kernel 5
+    where its tables fit, kernel 3 otherwise), each timed once.  Returns a dict."""
     def maxshift_of(c, f1, fo, ts, dm):
         p = dd.Plan(c, f1, fo, ts, [dm], [1], 6.0, dd.DD_F32, 1 << 30)
         m = p.maxshift
         p.close()
         return m
 
+    t_setup = time.perf_counter()
     beams = synth.batch_beams(24, 4, maxshift_of)
     widths = (1, 2, 4, 8, 16, 32)
     plans, ins, pitches, outs = [], [], [], []
@@ -482,14 +499,31 @@ def run_batch(args):
     adds = sum(p.ndm * p.nsamp_out * p.nchans for p in plans)
     stream = torch.cuda.Stream()
     batch = dd.Batch(plans)
-    batch.autotune(ins, pitches, outs, stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    if full_autotune:
+        batch.autotune(ins, pitches, outs, stream)
+        how = "the batch autotuner's choice over every configuration and both launch modes"
+    else:
+        best = None
+        for per_beam in (True, False):
+            batch.set_launch_mode(per_beam)
+            batch.execute(ins, pitches, outs, stream)            # warm-up
+            ev[0].record(stream)
+            batch.execute(ins, pitches, outs, stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            ms = ev[0].elapsed_time(ev[1])
+            if best is None or ms < best[0]:
+                best = (ms, per_beam)
+        batch.set_launch_mode(best[1])
+        how = "default mixed configuration (kernel 5 / kernel 3), the faster launch mode of one timed run each"
     batch.capture(ins, pitches, outs, stream)
     # the sequential reference runs each plan with the tile shape it has in the batch
     beam_cfg = [batch.beam_config(i) for i in range(len(plans))]
     for p, c in zip(plans, beam_cfg):
         if c >= 0:
             p.set_tile(c, 8)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    setup_s = time.perf_counter() - t_setup
 
     def run_batch_once():
         batch.launch(stream)
@@ -505,150 +539,210 @@ def run_batch(args):
             tot += p.search(o, stream=stream, allow_overflow=True)[1]
         return tot
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         run_batch_once()
+    if sequential:
         run_sequential_once()
     torch.cuda.synchronize()
     tb, ts_ = [], []
-    for _ in range(args.steps):
+    for _ in range(steps):
         ev[0].record(stream)
         nb = run_batch_once()
         ev[1].record(stream)
-        ev[2].record(stream)
-        ns = run_sequential_once()
-        ev[3].record(stream)
         torch.cuda.synchronize()
         tb.append(ev[0].elapsed_time(ev[1]))
-        ts_.append(ev[2].elapsed_time(ev[3]))
-    mb, ms = statistics.median(tb), statistics.median(ts_)
+        if sequential:
+            ev[2].record(stream)
+            run_sequential_once()
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            ts_.append(ev[2].elapsed_time(ev[3]))
+    mb = statistics.median(tb)
     sm = torch.cuda.get_device_properties(0).multi_processor_count
     peak = sm * 128 * 2070e6 / 1e9
     cfg, nitems, nsep = batch.info
-    line = {
-        "mode": "batch", "metric": METRIC, "value": units / (mb / 1e3), "unit": METRIC,
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mb,
-        "higher_is_better": True, "dtype": "f32/u8", "data": "synthetic",
-        "config": {"workload": "24 uneven beams: 256-4096 ch, 2^16-2^20 samples, 500-4000 DMs, "
-                   "fp32 + uint8, widths 1..32, 6 sigma", "units": units, "adds": adds,
-                   "tile_config": cfg, "work_items": nitems, "separate_beams": nsep,
-                   "beams_on_kernel5": sum(1 for c in beam_cfg if c >= 9),
-                   "launch": ("each beam's own de-dispersion launch" if batch.per_beam else "persistent kernel")
-                             + " + per-beam search, CUDA graph replay (the batch autotuner's choice)"},
-        "sequential": {"value": units / (ms / 1e3), "ms_per_step": ms,
-                       "how": "each beam through dd_execute + dd_search in turn, its batch tile shape"},
-        "speedup_vs_sequential": ms / mb,
-        "candidates": int(nb),
+    res = {
+        "value": units / (mb / 1e3), "unit": METRIC, "ms_per_step": mb, "steps": steps, "warmup": warmup,
+        "workload": "24 uneven beams: 256-4096 ch, 2^16-2^20 samples, 500-4000 DMs, fp32 + uint8, "
+                    "widths 1..32, 6 sigma", "units": units, "adds": adds,
+        "tile_config": cfg, "work_items": nitems, "separate_beams": nsep,
+        "beams_on_kernel5": sum(1 for c in beam_cfg if c >= 9),
+        "launch": ("each beam's own de-dispersion launch" if batch.per_beam else "one persistent kernel")
+                  + " + per-beam search, CUDA graph replay",
+        "how_chosen": how, "candidates": int(nb),
         "achieved_gadd_s": adds / (mb / 1e3) / 1e9, "alu_frac_of_peak": adds / (mb / 1e3) / 1e9 / peak,
+        "setup_s": setup_s,
     }
-    print(json.dumps(line), flush=True)
+    if sequential:
+        ms = statistics.median(ts_)
+        res["sequential"] = {"value": units / (ms / 1e3), "ms_per_step": ms,
+                             "how": "each beam through dd_execute + dd_search in turn, its batch tile shape"}
+        res["speedup_vs_sequential"] = ms / mb
     batch.close()
     for p in plans:
         p.close()
+    del ins, outs
+    torch.cuda.synchronize()
+    return res
 
 
-def run_serve(args):
-    """64 streaming uint8 beams (1024/4096 channels, 1000-4096 DM trials to DM
-    500, chunks of 65536 samples) arriving at args.speed x the real-time rate
-    with +-10% jitter.  Beams are admitted against args.budget_frac of free device memory;
-    a beam that does not fit waits until a served beam leaves (each beam
-    streams its priming chunks + 3 searched chunks).  Prints one JSON line
-    (mode "serve") with throughput, p50/p99 chunk latency and real-time factor."""
+def run_batch(args):
+    """The batched workload alone: prints one JSON line (mode "batch")."""
     import torch
     import paper_1107_2516_gb300 as dd
     from paper_1107_2516_gb300 import build as ddbuild
 
     ddbuild.build()
     dd.load()
+    r = batch_measure(torch, dd, args.steps, args.warmup, full_autotune=not args.no_autotune)
+    line = {"mode": "batch", "metric": METRIC, "value": r.pop("value"), "unit": METRIC, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r.pop("ms_per_step"),
+            "higher_is_better": True, "dtype": "f32/u8", "data": "synthetic", "config": r}
+    print(json.dumps(line), flush=True)
+
+
+def serve_measure(torch, dd, window_s, speed, workers, budget_frac, burst):
+    """The 64-beam streaming workload (uint8, 1024/4096 channels, 1000-4096 DM
+    trials to DM 500, chunks of 65536 samples) on one server, in steady state.
+    Admission: every beam is admitted against budget_frac of free device
+    memory (a beam that does not fit waits for one to leave) and streams its
+    priming chunks at once (the history a live stream holds already).  Then
+    (1) real-time window: each beam's chunks arrive at `speed` x its real-time
+    rate (+-10% jitter, random phase) for window_s seconds: chunk latency
+    (submit -> candidates on the host) p50/p99 and the real-time factor (chunk
+    duration / processing time); (2) capacity: every served beam submits
+    `burst` chunks at once and the server runs them with its worker streams
+    (continuous batching): DM-trial.samples/s over the burst.  Returns a dict."""
     beams = synth.serve_beams(64, 5)
     free, _ = torch.cuda.mem_get_info()
-    budget = int(args.budget_frac * free)
-    srv = dd.Server(budget, nworkers=args.workers, max_candidates=1 << 16)
+    budget = int(budget_frac * free)
+    t_setup = time.perf_counter()
+    srv = dd.Server(budget, nworkers=workers, max_candidates=1 << 16)
     data = {c: torch.from_numpy(synth.quantize_u8(synth.noise_f32(c, 65536, seed=c))).pin_memory()
             for c in (1024, 4096)}
     widths = (1, 2, 4, 8, 16, 32, 64)
-    pending = list(range(len(beams)))
-    active = {}            # beam index -> dict(id, times, next, total, done, real)
-    refused_first = 0
-    lat, proc, rtf, units = [], [], [], 0
+    st = {}
+    refused = []
+    kernels = {}
+    for i, b in enumerate(beams):
+        try:
+            bid = srv.add_beam(b.nchans, b.fch1, b.foff, b.tsamp, b.dm_list, widths, 6.0, dd.DD_U8, b.chunk)
+        except dd.DDError as e:
+            if e.code != dd.dd.DD_ERR_BUDGET:
+                raise
+            refused.append(i)
+            continue
+        info = srv.beam_info(bid)
+        k = srv.beam_kernel(bid)[0]
+        kernels[k] = kernels.get(k, 0) + 1
+        prime = -(-info["maxshift"] // b.chunk)
+        st[bid] = dict(i=i, next=0, prime=prime, ndm=b.ndm, period=b.period, chunk=b.chunk)
+    for bid, s in st.items():
+        for q in range(s["prime"]):
+            srv.submit(bid, data[beams[s["i"]].nchans], s["chunk"], q)
+        s["next"] = s["prime"]
+    npr = sum(s["prime"] for s in st.values())
+    got = 0
+    while got < npr:
+        for r in srv.poll(max_results=256, wait_ms=100):
+            if int(r["status"]) != dd.DD_PRIMING:
+                raise RuntimeError(f"priming chunk status {int(r['status'])}")
+            got += 1
+    setup_s = time.perf_counter() - t_setup
+
+    # (1) real-time window
+    for bid, s in st.items():
+        b = beams[s["i"]]
+        s["times"] = synth.arrival_times(b, 64, b.seed) / speed
+    lat, proc, rtf, units_rt = [], [], [], 0
     t0 = time.perf_counter()
-    first_try = True
-
-    def admit(now):
-        nonlocal refused_first
-        still = []
-        for i in pending:
-            b = beams[i]
-            try:
-                bid = srv.add_beam(b.nchans, b.fch1, b.foff, b.tsamp, b.dm_list, widths, 6.0,
-                                   dd.DD_U8, b.chunk)
-            except dd.DDError as e:
-                if e.code != 6:
-                    raise
-                still.append(i)
-                continue
-            info = srv.beam_info(bid)
-            prime = -(-info["maxshift"] // b.chunk)
-            n = prime + 3
-            times = now + synth.arrival_times(b, n, b.seed) / args.speed
-            active[i] = dict(id=bid, times=times, next=0, total=n, done=0, real=0, ndm=b.ndm)
-        if first_try:
-            refused_first += len(still)
-        pending[:] = still
-
-    admit(0.0)
-    first_try = False
-    byid = {v["id"]: k for k, v in active.items()}
-    limit = args.serve_limit
-    while (active or pending) and time.perf_counter() - t0 < limit:
+    outstanding = 0
+    while True:
         now = time.perf_counter() - t0
         nxt = None
-        for i, st in active.items():
-            while st["next"] < st["total"] and st["times"][st["next"]] <= now:
-                srv.submit(st["id"], data[beams[i].nchans], beams[i].chunk, st["next"])
-                st["next"] += 1
-            if st["next"] < st["total"]:
-                ta = st["times"][st["next"]]
-                nxt = ta if nxt is None else min(nxt, ta)
+        if now < window_s:
+            for bid, s in st.items():
+                j = s["next"] - s["prime"]
+                while j < len(s["times"]) and s["times"][j] <= now:
+                    srv.submit(bid, data[beams[s["i"]].nchans], s["chunk"], s["next"])
+                    s["next"] += 1
+                    outstanding += 1
+                    j += 1
+                if j < len(s["times"]):
+                    nxt = s["times"][j] if nxt is None else min(nxt, s["times"][j])
+        elif outstanding == 0:
+            break
         wait = 50 if nxt is None else max(1, min(50, int((nxt - now) * 1000)))
         for r in srv.poll(max_results=256, wait_ms=wait):
-            i = byid[int(r["beam"])]
-            st = active[i]
-            st["done"] += 1
-            if int(r["status"]) == 0:
-                lat.append(float(r["t_done"] - r["t_submit"]))
-                pt = float(r["t_done"] - r["t_start"])
-                proc.append(pt)
-                rtf.append(beams[i].period / pt)
-                units += st["ndm"] * beams[i].chunk
-                st["real"] += 1
-            elif int(r["status"]) != dd.DD_PRIMING:
-                raise RuntimeError(f"chunk failed with status {int(r['status'])}")
-            if st["done"] == st["total"]:
-                srv.remove_beam(st["id"])
-                del active[i]
-                if pending:
-                    admit(time.perf_counter() - t0)
-                    byid = {v["id"]: k for k, v in active.items()}
-    wall = time.perf_counter() - t0
+            s = st[int(r["beam"])]
+            if int(r["status"]) != 0:
+                raise RuntimeError(f"chunk status {int(r['status'])}")
+            outstanding -= 1
+            lat.append(float(r["t_done"] - r["t_submit"]))
+            pt = float(r["t_done"] - r["t_start"])
+            proc.append(pt)
+            rtf.append(s["period"] / pt)
+            units_rt += s["ndm"] * s["chunk"]
+            srv.candidates(int(r["beam"]), int(r["seq"]), capacity=1 << 16)   # fetched (and freed)
+        if time.perf_counter() - t0 > window_s + 120:
+            raise RuntimeError("serving window did not drain")
+    wall_rt = time.perf_counter() - t0
+
+    # (2) capacity: `burst` chunks per beam submitted at once
+    units_b, lat_b = 0, []
+    t1 = time.perf_counter()
+    for bid, s in st.items():
+        for _ in range(burst):
+            srv.submit(bid, data[beams[s["i"]].nchans], s["chunk"], s["next"])
+            s["next"] += 1
+    left = burst * len(st)
+    while left:
+        for r in srv.poll(max_results=256, wait_ms=100):
+            if int(r["status"]) != 0:
+                raise RuntimeError(f"chunk status {int(r['status'])}")
+            s = st[int(r["beam"])]
+            units_b += s["ndm"] * s["chunk"]
+            lat_b.append(float(r["t_done"] - r["t_submit"]))
+            left -= 1
+        if time.perf_counter() - t1 > 600:
+            raise RuntimeError("burst did not drain")
+    wall_b = time.perf_counter() - t1
     srv.close()
     lat_a, rtf_a = np.array(lat), np.array(rtf)
-    line = {
-        "mode": "serve", "metric": METRIC, "value": units / wall, "unit": METRIC,
-        "n_gpus": 1, "higher_is_better": True, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "64 streaming uint8 beams, 1024/4096 ch, 1000-4096 DMs to DM 500, "
-                   "chunks of 65536 samples, widths 1..64, 6 sigma",
-                   "arrival": f"{args.speed}x real-time rate, +-10% jitter, random phase",
-                   "hbm_budget_bytes": budget, "workers": args.workers},
-        "chunks_searched": len(lat), "beams": len(beams),
-        "beams_refused_at_start_then_admitted": refused_first,
-        "beams_never_admitted": len(pending),
-        "latency_s": {"p50": float(np.percentile(lat_a, 50)) if len(lat) else None,
-                      "p99": float(np.percentile(lat_a, 99)) if len(lat) else None},
-        "processing_s": {"p50": float(np.percentile(proc, 50)) if proc else None},
-        "real_time_factor": {"median": float(np.median(rtf_a)) if len(rtf) else None,
-                             "min": float(rtf_a.min()) if len(rtf) else None},
-        "wall_s": wall,
+    periods = [beams[s["i"]].period for s in st.values()]
+    return {
+        "value": units_b / wall_b, "unit": METRIC,
+        "workload": "64 streaming uint8 beams, 1024/4096 ch, 1000-4096 DMs to DM 500, chunks of 65536 "
+                    "samples, widths 1..64, 6 sigma",
+        "hbm_budget_bytes": budget, "workers": workers, "beams_admitted": len(st),
+        "beams_refused_by_budget": len(refused), "beam_kernels": {str(k): v for k, v in sorted(kernels.items())},
+        "setup_s": setup_s,
+        "realtime": {"arrival": f"{speed}x real-time rate, +-10% jitter, random phase", "window_s": window_s,
+                     "chunks_searched": len(lat), "chunk_duration_s": [min(periods), max(periods)],
+                     "latency_s": {"p50": float(np.percentile(lat_a, 50)) if len(lat) else None,
+                                   "p99": float(np.percentile(lat_a, 99)) if len(lat) else None},
+                     "processing_s": {"p50": float(np.percentile(proc, 50)) if proc else None},
+                     "real_time_factor": {"median": float(np.median(rtf_a)) if len(rtf) else None,
+                                          "min": float(rtf_a.min()) if len(rtf) else None},
+                     "rate": units_rt / wall_rt, "wall_s": wall_rt},
+        "capacity": {"how": f"{burst} chunks per served beam submitted at once", "chunks": burst * len(st),
+                     "wall_s": wall_b, "value": units_b / wall_b,
+                     "latency_s": {"p50": float(np.percentile(lat_b, 50)), "p99": float(np.percentile(lat_b, 99))},
+                     "real_time_factor": (sum(burst * p for p in periods)) / wall_b},
     }
+
+
+def run_serve(args):
+    """The streaming workload alone: prints one JSON line (mode "serve")."""
+    import torch
+    import paper_1107_2516_gb300 as dd
+    from paper_1107_2516_gb300 import build as ddbuild
+
+    ddbuild.build()
+    dd.load()
+    r = serve_measure(torch, dd, args.serve_window, args.speed, args.workers, args.budget_frac, args.burst)
+    line = {"mode": "serve", "metric": METRIC, "value": r.pop("value"), "unit": METRIC, "n_gpus": 1,
+            "higher_is_better": True, "dtype": "u8", "data": "synthetic", "config": r}
     print(json.dumps(line), flush=True)
 
 
@@ -880,9 +974,12 @@ def main():
                          "realtime: the Section 5 pipeline (voltages -> front end -> de-dispersion)")
     ap.add_argument("--dms-per-nominal", type=int, default=24, help="subband: fine DMs per nominal DM")
     ap.add_argument("--nsub", type=int, default=32, help="subband: number of subbands")
-    ap.add_argument("--speed", type=float, default=4.0, help="serve: arrival rate / real-time rate")
+    ap.add_argument("--speed", type=float, default=1.0, help="serve: arrival rate / real-time rate")
     ap.add_argument("--workers", type=int, default=4, help="serve: server worker streams")
-    ap.add_argument("--serve-limit", type=float, default=240.0, help="serve: wall-clock limit (s)")
+    ap.add_argument("--serve-window", type=float, default=25.0, help="serve: real-time window (s)")
+    ap.add_argument("--burst", type=int, default=2, help="serve: chunks per beam in the capacity burst")
+    ap.add_argument("--no-batch-serve", action="store_true",
+                    help="lofar: skip the batched and serving measurements")
     ap.add_argument("--budget-frac", type=float, default=0.6, help="serve: HBM budget / free memory")
     ap.add_argument("--kernel", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -85,12 +85,19 @@ def aligned_pitch(nsamp: int, elem_bytes: int, align: int = 16) -> int:
 
 
 def noise_f32(nchans: int, nsamp: int, seed: int, pitch: Optional[int] = None) -> np.ndarray:
-    """Channel-major float32 N(0,1) noise, shape [nchans][pitch]; padding columns are 0."""
+    """Channel-major float32 N(0,1) noise, shape [nchans][pitch]; padding columns are 0.
+
+    Drawn as float64 normals and rounded to float32: numpy's float32 normal
+    sampler takes accept/reject decisions in single precision with the
+    platform's exp, and one decision that rounds differently on another
+    machine shifts the whole rest of the stream; the float64 sampler's
+    decisions agree across machines, so the same seed gives the same samples
+    on the x86 build host and the Arm GPU host."""
     pitch = nsamp if pitch is None else pitch
     rng = np.random.Generator(np.random.PCG64(seed))
     out = np.zeros((nchans, pitch), dtype=np.float32)
     for c in range(nchans):
-        out[c, :nsamp] = rng.standard_normal(nsamp, dtype=np.float32)
+        out[c, :nsamp] = rng.standard_normal(nsamp)
     return out
 
 

@@ -267,7 +267,18 @@ def test_small_workload_pulse_recovered():
     nout = wl.nsamp - m
     out = oracle.dedisperse(data, d, nout)
     mu, sg = oracle.stats(out)
-    assert abs(mu) < 0.2 and abs(sg - math.sqrt(wl.nchans)) < 0.1 * math.sqrt(wl.nchans)
+    # the mean: the pulse's samples each enter every DM row whose window holds
+    # them (counted exactly here), plus noise whose mean over a row's window
+    # of one channel has spread 1/sqrt(nout), summed over C channels
+    dp = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, [pulse.dm])[0][0]
+    hits = 0
+    for i in range(len(dms)):
+        for j in range(pulse.width):
+            t = pulse.t0 + dp + j - d[i]
+            hits += int(np.sum((t >= 0) & (t < nout)))
+    mu_pulse = pulse.amp * hits / (len(dms) * nout)
+    assert abs(mu - mu_pulse) < 4 * math.sqrt(wl.nchans / nout), (mu, mu_pulse)
+    assert abs(sg - math.sqrt(wl.nchans)) < 0.1 * math.sqrt(wl.nchans)
     cands = oracle.search(out, list(wl.widths), mu, sg, wl.sigma)
     best = cands[np.argmax(cands["snr"])]
     assert (int(best["dm_idx"]), int(best["t"]), int(best["width_idx"])) == (30, 4000, 2)
