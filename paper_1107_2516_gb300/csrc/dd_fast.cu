@@ -285,8 +285,9 @@ static void share_tables_db(const int32_t *delays, int D, int C, double foff, dd
 {
     T = ShareTables();
     constexpr int CS = kShCS, NP = kShNP;
-    const int TILE = 32 * kShareCfg[k].ti;
+    const int TILE = 32 * kShareCfg[k].ti, nw = kShareCfg[k].nw;
     using R = ShareRecDB<DB>;
+    if (nw > R::kMaxWarps) return;
     if (C % CS) return;
     const int S = C / CS, nblk = (D + DB - 1) / DB;
     const int AL = elem_align(dtype);
@@ -326,8 +327,8 @@ static void share_tables_db(const int32_t *delays, int D, int C, double foff, dd
                 need = std::max<long long>(need, (long long)(hi - b0) + TILE);
             }
             // patterns end to end in P; b_c without the row stride (added once rs is known)
-            int poff = 0;
-            std::vector<int> plo(pats.size()), pof(pats.size());
+            int poff = 0, rows = 0;
+            std::vector<int> plo(pats.size()), pof(pats.size()), prow(pats.size() + 1);
             for (int q = 0; q < (int)pats.size(); ++q) {
                 int lo = INT_MAX, hi = INT_MIN;
                 for (int j = 0; j < DB; ++j)
@@ -336,9 +337,22 @@ static void share_tables_db(const int32_t *delays, int D, int C, double foff, dd
                 int32_t *pr = t + R::kPat + q * R::kPatLen;
                 pr[0] = poff + W;
                 for (int cc = 0; cc < CS; ++cc) pr[1 + cc] = rowoff[cc] + lo + pats[q][cc] - poff;
+                pr[R::kPatStart] = poff;
+                pr[R::kPatRows] = rows;
                 plo[q] = lo;
                 pof[q] = poff;
+                prow[q] = rows;
                 poff += W;
+                rows += (W + 31) / 32;
+            }
+            prow[pats.size()] = rows;
+            // stage-1 split: warp w's first row and the pattern holding it
+            for (int w = 0; w <= nw; ++w) t[R::kWarp + w] = (int)((long long)w * rows / nw);
+            for (int w = 0; w < nw; ++w) {
+                const int r0 = t[R::kWarp + w];
+                int q = 0;
+                while (q + 1 < (int)pats.size() && prow[q + 1] <= r0) ++q;
+                t[R::kWarp + R::kMaxWarps + 1 + w] = q;
             }
             t[R::kE] = poff;
             pmax = std::max(pmax, poff);

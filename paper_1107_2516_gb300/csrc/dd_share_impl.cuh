@@ -16,9 +16,10 @@
 //            its trials need (P, double-buffered in shared memory).  The
 //            patterns' sums are laid end to end in one index space e < E,
 //            cut into rows of 32 (each row inside one pattern), and each warp
-//            sums a contiguous run of rows, four rows per step: the pattern's
-//            fields are uniform in the warp and reloaded only where a pattern
-//            ends, and every warp gets the same number of rows;
+//            sums the contiguous run of rows the table assigns it, four rows
+//            per step: the pattern's fields are uniform in the warp and
+//            reloaded only where a pattern ends, and every warp gets the same
+//            number of rows;
 //   stage 2: each warp adds, for its trials, P_pat[t + offset] (one
 //            conflict-free shared word per add, as kernel 3).
 // One __syncthreads per subband: stage 1 of subband s+1 writes the other P
@@ -36,19 +37,28 @@ namespace dd {
 // Table record of one (DM block, subband), int32 (16-byte multiple):
 //   [0 .. DB) q_j (index into P of trial j's t = t0 term) | [DB] E (the
 //   subband's P length) | 3 unused |
-//   per pattern p < NPMAX, kPatLen words: {end_p, b_0 .. b_{CS-1}, unused},
-// end_p = the index in P just past pattern p's sums, and b_c such that the
-// term of channel c in P[e] (e in pattern p) is staged element b_c + e of the
-// stage's rows (b_c = c * rs + the row offset of the pattern's first sample
-// minus the pattern's start in P).
+//   per pattern p < NPMAX, kPatLen words: {end_p, b_0 .. b_{CS-1}, start_p,
+//   rows_p, unused} |
+//   stage-1 split: [kWarp + w] (w <= kMaxWarps) first row of warp w (the
+//   row count R at w = the block's warp count), [kWarp + kMaxWarps + 1 + w]
+//   the pattern holding that row.
+// start_p / end_p = the index range of pattern p's sums in P; b_c such that
+// the term of channel c in P[e] (e in pattern p) is staged element b_c + e of
+// the stage's rows (b_c = c * rs + the row offset of the pattern's first
+// sample minus start_p); rows_p = the rows of 32 sums before pattern p (the
+// patterns' sums are cut into rows of 32, each row inside one pattern).
 template <int CS, int NPMAX, int DB>
 struct ShareRec {
     static_assert(DB % 4 == 0, "trial offsets are loaded 4 at a time");
+    static_assert(CS + 3 <= 8, "pattern record: end, CS row offsets, start, rows before");
     static constexpr int kTrial = 0;
     static constexpr int kE = DB;
     static constexpr int kPat = DB + 4;                 // first pattern field (16-byte aligned)
-    static constexpr int kPatLen = (1 + CS + 3) / 4 * 4;
-    static constexpr int kLen = kPat + NPMAX * kPatLen;
+    static constexpr int kPatLen = 8;
+    static constexpr int kPatStart = 1 + CS, kPatRows = 2 + CS;
+    static constexpr int kMaxWarps = 8;
+    static constexpr int kWarp = kPat + NPMAX * kPatLen;
+    static constexpr int kLen = kWarp + (2 * kMaxWarps + 1 + 3) / 4 * 4;
 };
 
 struct ShareLaunch {
@@ -69,34 +79,19 @@ struct ShareLaunch {
 
 // Stage 1 of one subband: P[e] for e < E (the patterns' sums end to end).
 // Each pattern's sums form rows of 32 consecutive e (the last one partial);
-// warp w takes the contiguous rows [w R / NW, (w+1) R / NW) of all R rows, so
-// a row's pattern (its fields) is uniform in the warp and changes only at
-// pattern ends, and lane l sums element row_start + l of each of its rows,
-// four rows at a time.
-template <typename Tin, typename R, int CS, int NW, int NPMAX>
+// warp w takes the contiguous rows the record assigns it (the host splits
+// the R rows evenly, w R / NW onwards), so a row's pattern (its fields) is
+// uniform in the warp and changes only at pattern ends, and lane l sums
+// element row_start + l of each of its rows: whole rows four at a time with
+// the pattern's offsets set up once, the pattern's partial last row alone.
+template <typename Tin, typename R, int CS, int NW>
 __device__ __forceinline__ void share_stage1(const int32_t *rec, const Tin *srow, float *Pb, int warp, int lane)
 {
-    static_assert(NPMAX <= 32, "one pattern per lane");
-    const int E = rec[R::kE];
-    // lane p < npat: pattern p's end, start, rows; unused slots hold end 0
-    int end_p = lane < NPMAX ? rec[R::kPat + lane * R::kPatLen] : 0;
-    const int npat = __ffs(__ballot_sync(~0u, lane < NPMAX && end_p == E));
-    int start_p = __shfl_up_sync(~0u, end_p, 1);
-    if (lane == 0) start_p = 0;
-    const int rows_p = lane < npat ? (end_p - start_p + 31) >> 5 : 0;
-    int incl = rows_p;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(~0u, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const int rtot = __shfl_sync(~0u, incl, 31);
-    const int r1 = (warp + 1) * rtot / NW;
-    int r = warp * rtot / NW;
-    int p = __ffs(__ballot_sync(~0u, incl > r)) - 1;
+    static_assert(NW <= R::kMaxWarps, "stage-1 split recorded for at most kMaxWarps warps");
+    int r = rec[R::kWarp + warp];
+    const int r1 = rec[R::kWarp + warp + 1];
+    int p = rec[R::kWarp + R::kMaxWarps + 1 + warp];
     while (r < r1) {
-        const int pincl = __shfl_sync(~0u, incl, p), pst = __shfl_sync(~0u, start_p, p);
-        const int pend = __shfl_sync(~0u, end_p, p), pexcl = pincl - __shfl_sync(~0u, rows_p, p);
         const int32_t *pr = rec + R::kPat + p * R::kPatLen;
         int b[R::kPatLen];
 #pragma unroll
@@ -104,17 +99,31 @@ __device__ __forceinline__ void share_stage1(const int32_t *rec, const Tin *srow
             const int4 x = *reinterpret_cast<const int4 *>(pr + v);
             b[v] = x.x; b[v + 1] = x.y; b[v + 2] = x.z; b[v + 3] = x.w;
         }
-        const int rend = min(r1, pincl);
-        for (; r < rend; r += 4) {
+        const int pend = b[0], pst = b[R::kPatStart], pexcl = b[R::kPatRows];
+        const int rend = min(r1, pexcl + ((pend - pst + 31) >> 5));
+        const int rfull = min(rend, pexcl + ((pend - pst) >> 5));    // rows wholly inside the pattern
+        // row r's element for this lane: e = e0 + 32 r
+        const int e0 = pst - (pexcl << 5) + lane;
+        int src[CS];                                                   // staged element of channel c at e0
+#pragma unroll
+        for (int c = 0; c < CS; ++c) src[c] = b[1 + c] + e0;
+        for (; r + 4 <= rfull; r += 4) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int e = pst + ((r + u - pexcl) << 5) + lane;
-                if (r + u < rend && e < pend) {
-                    float v = lane_ld<Tin>(srow + b[1] + e);
+                const int o = (r + u) << 5;
+                float v = lane_ld<Tin>(srow + (src[0] + o));
 #pragma unroll
-                    for (int c = 1; c < CS; ++c) v += lane_ld<Tin>(srow + b[1 + c] + e);
-                    Pb[e] = v;
-                }
+                for (int c = 1; c < CS; ++c) v += lane_ld<Tin>(srow + (src[c] + o));
+                Pb[e0 + o] = v;
+            }
+        }
+        for (; r < rend; ++r) {
+            const int o = r << 5;
+            if (e0 + o < pend) {
+                float v = lane_ld<Tin>(srow + (src[0] + o));
+#pragma unroll
+                for (int c = 1; c < CS; ++c) v += lane_ld<Tin>(srow + (src[c] + o));
+                Pb[e0 + o] = v;
             }
         }
         r = rend;
@@ -268,7 +277,7 @@ __device__ __forceinline__ bool share_tile(const ShareLaunch &a, int blk, int64_
         const Tin *srow = rows + (size_t)buf * stage_elems;
         float *Pb = P + (size_t)(s & 1) * a.pmax;
         // stage 1: every pattern's partial sum over the samples its trials need
-        share_stage1<Tin, R, CS, NW, NPMAX>(rec, srow, Pb, warp, lane);
+        share_stage1<Tin, R, CS, NW>(rec, srow, Pb, warp, lane);
         // this warp's trials: index of their t = t0 term in P
 #pragma unroll
         for (int j = 0; j < DR; j += 4) {

@@ -18,6 +18,7 @@ from paper_1107_2516_gb300 import build as ddbuild
 from paper_1107_2516_gb300 import dd as ddc
 
 CS = 4
+NPMAX, MAXW = 16, 8          # pattern slots per record; warps the stage-1 split records
 SHAPES = {9: (512, 32), 10: (256, 32), 11: (512, 48)}     # config: (tile, trials per block)
 
 
@@ -53,7 +54,7 @@ def emulate(x, nsamp, d, foff, dtype, config):
                     stage[c * rs:c * rs + n] = x[s * CS + c, g:g + n]
                 r = rec[b, s]
                 E = int(r[db])
-                pats = r[db + 4:].reshape(-1, 8)
+                pats = r[db + 4:db + 4 + NPMAX * 8].reshape(-1, 8)
                 ends = pats[:, 0]
                 e = np.arange(E)
                 p = np.searchsorted(ends[ends > 0], e, side="right")
@@ -119,19 +120,26 @@ def test_kernel5_tables_bad_config():
 def _stage1_rows(rec_row, db, nw):
     """Kernel 5's stage-1 work split, restated: the patterns' sums (index space
     e < E) cut into rows of 32 inside each pattern; warp w of nw takes rows
-    [w R / nw, (w+1) R / nw) and lane l element row_start + l of each.  Returns
-    (how often each e is summed, every e's pattern matches its row's)."""
+    [w R / nw, (w+1) R / nw) and lane l element row_start + l of each.  The
+    record's per-pattern start / rows-before fields and per-warp first row and
+    pattern must be exactly these.  Returns how often each e is summed."""
     E = int(rec_row[db])
-    ends = rec_row[db + 4:].reshape(-1, 8)[:, 0].astype(np.int64)
+    pat = rec_row[db + 4:db + 4 + NPMAX * 8].reshape(NPMAX, 8).astype(np.int64)
+    ends = pat[:, 0]
     npat = int(np.nonzero(ends == E)[0][0]) + 1
     starts = np.concatenate([[0], ends[:npat - 1]])
     rows = (ends[:npat] - starts + 31) // 32
     incl = np.cumsum(rows)
     excl = incl - rows
+    assert np.array_equal(pat[:npat, 1 + CS], starts) and np.array_equal(pat[:npat, 2 + CS], excl)
     R = int(incl[-1])
+    wt = rec_row[db + 4 + NPMAX * 8:].astype(np.int64)
     cover = np.zeros(E, np.int64)
     for w in range(nw):
         r0, r1 = w * R // nw, (w + 1) * R // nw
+        assert wt[w] == r0 and wt[w + 1] == r1
+        if r0 < r1:
+            assert wt[MAXW + 1 + w] == int(np.searchsorted(incl, r0, side="right"))
         for r in range(r0, r1):
             p = int(np.searchsorted(incl, r, side="right"))
             e = starts[p] + 32 * (r - excl[p]) + np.arange(32)
