@@ -800,8 +800,10 @@ int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStre
     if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return set_error(DD_ERR_CUDA, "cudaEventCreate"); }
     float best = 1e30f;
     int bk = f->active, bg = f->dgroup, rc = DD_OK;
-    // largest raster group first: on a tie (within 0.5%) it keeps the least DRAM traffic
-    const int groups[] = {16, 8, 4};
+    // largest raster group first: on a tie (within 0.5%) it keeps the least DRAM
+    // traffic (64: every DM block of the usual plans in one group, each time
+    // tile's blocks together)
+    const int groups[] = {64, 16, 8, 4};
     // kernels 5, 3 and 2, each in its order of measured speed, so that a tie
     // keeps the earlier one (kernel 5's 48-trial shape first: fewest input
     // re-reads); kernel 4 (slower on every plan measured) runs only on request
@@ -812,7 +814,7 @@ int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStre
         if (rc != DD_OK) break;
         if (!cfg_ok(f, k)) continue;
         rc = fast_run(p, k, 8, in, pitch, out, s);             // warm-up (caches, clocks)
-        for (int gi = 0; gi < 3 && rc == DD_OK; ++gi) {
+        for (int gi = 0; gi < 4 && rc == DD_OK; ++gi) {
             cudaEventRecord(e0, s);
             rc = fast_run(p, k, groups[gi], in, pitch, out, s);
             cudaEventRecord(e1, s);

@@ -152,7 +152,7 @@ __device__ __forceinline__ void share_store(const ShareLaunch &a, const float (&
                 const int64_t t = t0 + lane + 32 * i;
                 if (dm < a.ndm && t < nout) {
                     const long long v = __float2int_rn(acc[j][i]);
-                    out[(size_t)dm * nout + t] = (int32_t)v;
+                    __stcs(&out[(size_t)dm * nout + t], (int32_t)v);
                     st.n++; st.s += v; st.q += (unsigned long long)(v * v);
                 }
             }
@@ -166,7 +166,7 @@ __device__ __forceinline__ void share_store(const ShareLaunch &a, const float (&
             for (int i = 0; i < TI; ++i) {
                 const int64_t t = t0 + lane + 32 * i;
                 if (dm < a.ndm && t < nout) {
-                    out[(size_t)dm * nout + t] = acc[j][i];
+                    __stcs(&out[(size_t)dm * nout + t], acc[j][i]);   // streamed: read back only by the search
                     st.n++; st.s += acc[j][i];
                 }
             }
@@ -238,13 +238,14 @@ __device__ __forceinline__ bool share_tile(const ShareLaunch &a, int blk, int64_
         mbar_arrive_tx(&bar[buf], bytes);
         bulk_g2s(srec + (size_t)buf * R::kLen, brec + (size_t)s * R::kLen, (uint32_t)(R::kLen * sizeof(int32_t)),
                  &bar[buf]);
+        const uint64_t pol = l2_evict_last();          // other DM blocks of this tile stage these rows soon
 #pragma unroll
         for (int cc = 0; cc < CS; ++cc) {
             int64_t g;
             const uint32_t nb = row_bytes(rb[cc], g);
             if (nb)
-                bulk_g2s(rows + (size_t)buf * stage_elems + (size_t)cc * rs,
-                         in + (size_t)(s * CS + cc) * a.pitch + g, nb, &bar[buf]);
+                bulk_g2s_hint(rows + (size_t)buf * stage_elems + (size_t)cc * rs,
+                              in + (size_t)(s * CS + cc) * a.pitch + g, nb, &bar[buf], pol);
         }
     };
     int rb[CS];

@@ -184,7 +184,7 @@ def test_autotune_keeps_parity():
     out = torch.empty(wl.ndm * plan.nsamp_out, dtype=torch.float32, device="cuda")
     plan.autotune(x, wl.nsamp, out)
     cfg, group, tr, nw = plan.tile
-    assert cfg in (0, 1, 2, 3, 4, 5, 6, 9, 10, 11) and group in (4, 8, 16) and tr in (8, 16, 20, 28, 36) \
+    assert cfg in (0, 1, 2, 3, 4, 5, 6, 9, 10, 11) and group in (4, 8, 16, 64) and tr in (8, 16, 20, 28, 36) \
         and nw in (4, 6, 8, 12)
     plan.execute(x, wl.nsamp, out)
     torch.cuda.synchronize()

@@ -177,3 +177,4 @@ def test_stage1_rows_cover_every_sum_once_lofar():
         for b in range(rec.shape[0]):
             for s in range(0, rec.shape[1], 16):
                 assert np.all(_stage1_rows(rec[b, s], db, nw) == 1), (config, b, s)
+
