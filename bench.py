@@ -37,10 +37,16 @@ WORKLOAD = "lofar_f32"
 # ncu DRAM bytes (read + write) per de-dispersion launch, keyed by the
 # (tile configuration, raster group) the capture used, with the digest of the
 # kernel's source files at capture time (kernel_source_digest): the figure is
-# reported only while the sources are unchanged.  Empty: the captures in
-# profiles/ (21.41 GB for config 11, 25.63 GB for config 5) predate edits to
-# those kernels.
-PROFILED_TRAFFIC = {}
+# reported only while the sources are unchanged.  Kernel 5 was captured on a
+# slice of the benchmark plan (all 2000 DM trials, 2^17 input samples: 217 of
+# the full plan's 2009 time tiles, 0.54 GB in, 0.89 GB out) and scaled to the
+# full launch: reads by the tile count (9.2581x), writes by the output count
+# (9.2901x); profiles/dedisp_kernel5_lofar_f32.md has the capture.
+PROFILED_TRAFFIC = {
+    (11, 64): (20093572595, "a0cee00b08184e2a30729436d717ee7cff822e8fef95e64909ab2aa65407cd52"),
+    (11, 16): (22283401405, "a0cee00b08184e2a30729436d717ee7cff822e8fef95e64909ab2aa65407cd52"),
+    (9, 64): (21270580135, "a0cee00b08184e2a30729436d717ee7cff822e8fef95e64909ab2aa65407cd52"),
+}
 KERNEL_SOURCES = {3: ("dd_lane_impl.cuh", "dd_lane_c2.cu", "dd_device.cuh", "dd_fast_impl.cuh"),
                   5: ("dd_share_impl.cuh", "dd_share.cu", "dd_lane_impl.cuh", "dd_device.cuh", "dd_fast_impl.cuh")}
 
