@@ -67,8 +67,15 @@ def test_per_row_statistics_match_oracle(dtype, widths):
             snr = (cj["value"] - w * mu_g[j]) / (sg_g[j] * np.sqrt(w))
             assert np.allclose(cj["snr"], snr, rtol=1e-5, atol=1e-4)
     assert gray <= 2
+    # the strongest candidate is the oracle's, on the pulse's DM and
+    # overlapping it (with widths 3 and 7 several windows of the 4-sample
+    # pulse hold the same signal; the noise decides between them)
     best = cands[np.argmax(cands["snr"])]
-    assert (int(best["dm_idx"]), int(best["t"])) == (30, 4000)
+    best_o = c_o[np.argmax(c_o["snr"])]
+    key = (int(best["dm_idx"]), int(best["t"]), int(best["width_idx"]))
+    assert key == (int(best_o["dm_idx"]), int(best_o["t"]), int(best_o["width_idx"]))
+    w = widths[key[2]]
+    assert key[0] == 30 and key[1] <= 4000 + 3 and key[1] + w - 1 >= 4000
     # whole-buffer statistics are restored
     plan.set_search_stats(False)
     c2, n2 = plan.search(out, capacity=1 << 18)
