@@ -19,6 +19,7 @@ pytestmark = pytest.mark.gpu
 
 import paper_1107_2516_gb300 as dd
 from paper_1107_2516_gb300 import build as ddbuild
+from paper_1107_2516_gb300 import dd as ddc
 
 DTYPES = {"f32": dd.DD_F32, "u8": dd.DD_U8, "f16": dd.DD_F16}
 
@@ -222,13 +223,31 @@ def test_edge_shapes(case, dtype):
     tsamp = 327.68e-6
     _, m = oracle.delays(nch, fch1, foff, tsamp, dms)
     nsamp = m + extra
-    pitch = nsamp + pad
-    for kernel in (0, 1, 3, 4, 5):
-        try:
-            run_case(nch, fch1, foff, tsamp, nsamp, dms, widths, 3.0, dtype, seed=case + 100,
-                     pitch=pitch, kernel=kernel, max_gray=2)
-        except dd.DDError as e:
-            assert kernel >= 3 and e.code == 1      # kernel unavailable for this plan
+    d_o, _ = oracle.delays(nch, fch1, foff, tsamp, dms)
+    k5_tables = any(ddc.dd_share_tables(np.asarray(d_o), foff, DTYPES[dtype], c) is not None for c in (9, 10, 11))
+    al = 4 if dtype == "f32" else 16
+    # the shape's own pitch (often not 16-byte aligned: the tiled kernels then
+    # fall back to kernel 1) and the next aligned one (the tiled kernels run)
+    for pitch in sorted({nsamp + pad, synth.aligned_pitch(nsamp + pad, 4 if dtype == "f32" else 1)}):
+        ran = {}
+        for kernel in (0, 1, 3, 4, 5):
+            try:
+                *_, used = run_case(nch, fch1, foff, tsamp, nsamp, dms, widths, 3.0, dtype, seed=case + 100,
+                                    pitch=pitch, kernel=kernel, max_gray=2)
+            except dd.DDError as e:
+                assert kernel >= 3 and e.code == 1      # kernel unavailable for this plan
+                ran[kernel] = None
+                continue
+            # the tiled kernels need 16-byte aligned rows; other pitches run kernel 1
+            ran[kernel] = used if used == 1 or pitch % al == 0 else 1
+            assert kernel == 0 or used == kernel, (kernel, used)
+        assert ran[1] == 1 and ran[0] in (1, 2, 3)
+        if pitch % al == 0:
+            assert ran[3] == 3                           # every edge shape has kernel-3 tables
+        if not k5_tables:
+            assert ran[5] is None                        # more delay patterns than a record holds
+        print(f"edge case {case} {dtype} pitch {pitch}: kernels run {ran} "
+              f"(kernel-5 tables {'yes' if k5_tables else 'no'})")
 
 
 
@@ -330,6 +349,17 @@ def test_process_host_pipelined(dtype, kernel, tile):
     else:
         assert abs(mu1 - mu2) <= 1e-12 * max(1.0, abs(mu2)) and abs(sg1 - sg2) <= 1e-12 * sg2
         assert np.max(np.abs(c1["snr"].astype(np.float64) - c2["snr"])) <= 1e-4
+    # and the host path against the oracle: statistics and candidate list
+    d_o, m_o = oracle.delays(lw.nchans, lw.fch1, lw.foff, lw.tsamp, dms)
+    ora = oracle.dedisperse(arr, d_o, plan.nsamp_out)
+    mu_o, sg_o = oracle.stats(ora)
+    if dtype == "u8":
+        assert abs(mu1 - mu_o) <= 1e-12 * max(1.0, abs(mu_o)) and abs(sg1 - sg_o) <= 1e-12 * sg_o
+    else:
+        assert abs(mu1 - mu_o) <= fp_tol(lw.nchans) and abs(sg1 - sg_o) <= 1e-5 * sg_o
+    eps = 0.0 if dtype == "u8" else fp_tol(lw.nchans)
+    n_match, n_gray = compare_candidates(c1, ora, [1, 2, 4, 8, 16], mu1, sg1, mu_o, sg_o, 4.0, eps)
+    assert n_match > 100 and n_gray <= 2, (n_match, n_gray)
     plan.close()
 
 

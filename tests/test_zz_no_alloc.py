@@ -6,11 +6,13 @@ another runtime).  This file is collected last so that a run stopping at the
 first failure has already run every other test.  The test calls the entry
 point through the C ABI twice in a row on the same buffer and compares each
 result with the statistics the plan-based path (dd_execute + dd_search)
-reports, within the tolerance the parity tests use.
+reports, within the tolerance the parity tests use, and with the FP64
+oracle's statistics of the same float32 values.
 """
 import numpy as np
 import pytest
 
+import oracle
 import synth
 from ddhelpers import fp_tol, make_input
 
@@ -35,6 +37,8 @@ def test_noalloc_stats_match_plan_stats_twice():
     plan.search(out)
     mu_ref, sg_ref = plan.stats()
     res = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    # the FP64 oracle's two-pass statistics of exactly these float32 values
+    mu_o, sg_o = oracle.stats(out.cpu().numpy().astype(np.float64))
     for _ in range(2):
         res.fill_(float("nan"))
         dd.dd_stats_f32_noalloc(out, out.numel(), res)
@@ -42,6 +46,8 @@ def test_noalloc_stats_match_plan_stats_twice():
         mu, sg = (float(v) for v in res.cpu())
         assert abs(mu - mu_ref) <= fp_tol(wl.nchans)
         assert abs(sg - sg_ref) <= 1e-5 * sg_ref
+        # per-thread partials of 16 values are FP32: relative error ~1e-7 each
+        assert abs(mu - mu_o) <= 1e-6 * sg_o and abs(sg - sg_o) <= 1e-6 * sg_o
     # a buffer beyond the fixed scratch is refused before any launch
     with pytest.raises(dd.DDError) as e:
         dd.dd_stats_f32_noalloc(out, (1 << 28) + 1, res)
