@@ -180,9 +180,10 @@ DD_API int dd_process_host(dd_plan *plan, const void *in_host, int64_t in_pitch,
                     void *stream);
 
 /* Select the de-dispersion kernel for a plan: 0 = automatic (default: the
- * first available of tile configurations 5, 3, 6, 4, 1, 0, 2 — kernel 3
- * shapes before kernel 2 shapes, in the order of measured speed — or the
- * autotuner's choice; kernel 1 if no tiled configuration fits),
+ * first available of tile configurations 11, 9, 10, 5, 3, 6, 4, 1, 0, 2 —
+ * kernel 5 shapes where their tables fit the plan, then kernel 3 and kernel 2
+ * shapes, in the order of measured speed — or the autotuner's choice;
+ * kernel 1 if no tiled configuration fits),
  * 1 = generic shared-memory kernel, 2 = register-blocked kernel (window
  * reused across 4 DM trials per thread), 3 = lane-interleaved kernel (one
  * conflict-free shared load per add, no branches), 4 = tensor-memory window

@@ -551,8 +551,10 @@ int fast_configure(dd_plan *p)
     if (rc == DD_OK && e != cudaSuccess) rc = cuda_fail(e, "kernel 2 setup");
     if (rc != DD_OK) { fast_release(p); return rc; }
     // default: the first available configuration in the order of measured
-    // speed (kernel 3 shapes, then kernel 2); the autotuner may change it
-    static const int pref[] = {kNumFastCfg + 2, kNumFastCfg + 0, kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
+    // speed (kernel 5 shapes where their tables fit, then kernel 3, then
+    // kernel 2); the autotuner may change it
+    static const int pref[] = {kShareBeg + 2, kShareBeg + 0, kShareBeg + 1, kNumFastCfg + 2, kNumFastCfg + 0,
+                               kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
     for (int k : pref)
         if (cfg_ok(f, k)) { f->active = k; break; }
     if (f->active < 0) { fast_release(p); return DD_OK; }   // tiled kernels unavailable

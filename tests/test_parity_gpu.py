@@ -98,7 +98,7 @@ def test_small_workload_parity(dtype, kernel):
     cands, out, ora, res, used = run_case(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.nsamp,
                                           wl.dm_list, wl.widths, wl.sigma, dtype, seed=wl.seed,
                                           pulses=small_pulse(), kernel=kernel)
-    assert used == (kernel or 3)           # default: kernel 3's fastest shape
+    assert used == (kernel or 3)           # default: kernel 5 cannot run this plan, so kernel 3
     best = cands[np.argmax(cands["snr"])]
     assert (int(best["dm_idx"]), int(best["t"]), int(best["width_idx"])) == (30, 4000, 2)
 
@@ -241,7 +241,7 @@ def test_edge_shapes(case, dtype):
             # the tiled kernels need 16-byte aligned rows; other pitches run kernel 1
             ran[kernel] = used if used == 1 or pitch % al == 0 else 1
             assert kernel == 0 or used == kernel, (kernel, used)
-        assert ran[1] == 1 and ran[0] in (1, 2, 3)
+        assert ran[1] == 1 and ran[0] in (1, 2, 3, 5)
         if pitch % al == 0:
             assert ran[3] == 3                           # every edge shape has kernel-3 tables
         if not k5_tables:
