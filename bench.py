@@ -76,7 +76,10 @@ def profiled_traffic(kernel_id: int, tile):
 # DM trials per thread or warp, warps per block)
 TILE_CONFIGS = {0: (2, 36, 4, 8), 1: (2, 20, 4, 12), 2: (2, 28, 4, 8), 3: (3, 16, 4, 8),
                 4: (3, 16, 8, 8), 5: (3, 16, 8, 4), 6: (3, 8, 16, 4), 7: (4, 20, 4, 8),
-                8: (4, 12, 8, 8), 9: (5, 16, 8, 4), 10: (5, 8, 8, 4), 11: (5, 16, 8, 6)}
+                8: (4, 12, 8, 8), 9: (5, 16, 8, 4), 10: (5, 8, 8, 4), 11: (5, 16, 8, 6),
+                12: (5, 16, 8, 8)}
+# warp-specialised kernel 5 shapes: their stage-1 warps (beside the warps above)
+STAGE1_WARPS = {12: 8}
 
 
 # ------------------------------------------------------------------ replicas (N > 1)
@@ -383,7 +386,9 @@ def run_ours(args, rank, world, local_rank):
         k, ns, nd, nw = TILE_CONFIGS[tile[0]]
         per = "thread" if k == 2 else "lane"
         tile_s = (f", tile config {tile[0]}: {ns} samples per {per} x {nd} DM trials per "
-                  f"{'thread' if k == 2 else 'warp'}, {nw} warps, raster group {tile[1]}")
+                  f"{'thread' if k == 2 else 'warp'}, {nw} warps"
+                  + (f" + {STAGE1_WARPS[tile[0]]} stage-1 warps" if tile[0] in STAGE1_WARPS else "")
+                  + f", raster group {tile[1]}")
     roof = {"bound": "alu", "kernel": f"dd kernel {kernel_id} (de-dispersion{tile_s})",
             "achieved": achieved, "peak": peak, "unit": "Gadd/s", "frac": achieved / peak,
             "peak_basis": f"{sm} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (max clock)",

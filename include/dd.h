@@ -180,7 +180,7 @@ DD_API int dd_process_host(dd_plan *plan, const void *in_host, int64_t in_pitch,
                     void *stream);
 
 /* Select the de-dispersion kernel for a plan: 0 = automatic (default: the
- * first available of tile configurations 11, 9, 10, 5, 3, 6, 4, 1, 0, 2 —
+ * first available of tile configurations 11, 12, 9, 10, 5, 3, 6, 4, 1, 0, 2 —
  * kernel 5 shapes where their tables fit the plan, then kernel 3 and kernel 2
  * shapes, in the order of measured speed — or the autotuner's choice;
  * kernel 1 if no tiled configuration fits),
@@ -201,7 +201,7 @@ DD_API int dd_plan_set_kernel(dd_plan *plan, int32_t kernel);
 DD_API int dd_plan_get_kernel(const dd_plan *plan, int32_t *kernel);
 
 /* Autotuner for the tiled kernels: runs the plan on the caller's buffers
- * once per compiled tile configuration of kernels 2, 3 and 5 (0-6, 9-11,
+ * once per compiled tile configuration of kernels 2, 3 and 5 (0-6, 9-12,
  * see dd_plan_set_tile) and raster group, times each with CUDA events on
  * `stream`, keeps the fastest for this plan and caches the choice
  * process-wide for plans of the same shape.  Kernel 4 is not timed (slower on
@@ -219,7 +219,10 @@ DD_API int dd_plan_autotune(dd_plan *plan, const void *in_dev, int64_t in_pitch,
  * 5: 16 x 8, 4 warps; 6: 8 x 16, 4 warps; kernel 4 (samples per lane x DM
  * trials per warp, warps) — 7: 20 x 4, 8 warps; 8: 12 x 8, 8 warps; kernel
  * 5 (samples per lane x DM trials per warp, warps; 4-channel subbands) — 9:
- * 16 x 8, 4 warps; 10: 8 x 8, 4 warps; 11: 16 x 8, 6 warps};
+ * 16 x 8, 4 warps; 10: 8 x 8, 4 warps; 11: 16 x 8, 6 warps; 12: 16 x 8, 8
+ * warps that add the partial sums beside 8 warps that form them (one block
+ * per SM, the two groups joined by mbarriers; available where the GPU's
+ * compiled register count covers the split)};
  * raster_group (>= 1) is the number of DM blocks whose time tiles are swept
  * together.  DD_ERR_ARG if the configuration cannot run this plan. */
 DD_API int dd_plan_set_tile(dd_plan *plan, int32_t config, int32_t raster_group);
@@ -284,7 +287,7 @@ DD_API int dd_batch_autotune(dd_batch *batch, const void *const *in_devs, const 
 DD_API int dd_host_chunk_schedule(int64_t nsamp_out, int64_t pitch, int32_t tile, int64_t reach,
                                   int64_t *col_end, int64_t *tile_end, int32_t *n);
 
-/* Kernel 5's tables for tile configuration `config` (9-11) of a delay table
+/* Kernel 5's tables for tile configuration `config` (9-12) of a delay table
  * delays[ndm][nchans] (dd_plan_info's copy), computed on the host (no device
  * needed), for inspection and tests.  info[6] receives {1 if the shape can
  * run the table (at most 16 delay patterns per block and subband) else 0,
@@ -294,11 +297,12 @@ DD_API int dd_host_chunk_schedule(int64_t nsamp_out, int64_t pitch, int32_t tile
  * each trial's partial-sum index of its first sample; [trials]: the
  * subband's partial-sum length E; from trials + 4, 8 words per pattern:
  * {end of its sums in the partial-sum buffer, then per channel c of the
- * subband the staged element of its first term minus its start} — and the
- * staged row starts int32 [blocks][nchans] relative to a tile's first
- * output sample.  foff's sign picks the subband reference channel (the
- * highest frequency).  DD_ERR_ARG for another configuration or too small a
- * capacity. */
+ * subband the staged element of its first term minus its start} — and
+ * int32 [2][blocks][nchans]: the staged row starts relative to a tile's
+ * first output sample, then the staged row lengths (the elements the block's
+ * trials read, in 16-byte units; at most rs).  foff's sign picks the subband
+ * reference channel (the highest frequency).  DD_ERR_ARG for another
+ * configuration or too small a capacity. */
 DD_API int dd_share_tables(const int32_t *delays, int32_t ndm, int32_t nchans, double foff, int32_t dtype,
                            int32_t config, int32_t *info, int32_t *rec_out, int64_t rec_cap, int32_t *base_out,
                            int64_t base_cap);

@@ -55,7 +55,7 @@ struct ShareCfgData {
     int64_t reach = 0;           // input columns a tile at t0 reads lie below t0 + reach
     size_t smem = 0;
     int32_t *d_rec = nullptr;    // [nblk][nsub][kLen] subband records
-    int32_t *d_base = nullptr;   // [nblk][nchans] staged row starts
+    int32_t *d_base = nullptr;   // [2][nblk][nchans] staged row starts, then staged row lengths
 };
 
 // Tile configurations: indices [0, kNumFastCfg) are kernel 2 shapes,
@@ -274,7 +274,7 @@ static void free_share(ShareCfgData &c)
 // staged row start; T.ok stays false if a (block, subband) has more than
 // kShNP delay patterns.
 struct ShareTables {
-    std::vector<int32_t> rec, base;
+    std::vector<int32_t> rec, base;   // base: [2][nblk][nchans] row starts, then row lengths
     int nblk = 0, nsub = 0, rs = 0, pmax = 0, klen = 0;
     bool ok = false;
 };
@@ -285,13 +285,15 @@ static void share_tables_db(const int32_t *delays, int D, int C, double foff, dd
 {
     T = ShareTables();
     constexpr int CS = kShCS, NP = kShNP;
-    const int TILE = 32 * kShareCfg[k].ti, nw = kShareCfg[k].nw;
+    // the stage-1 split goes to the warps that run stage 1 (the stage-1 warps
+    // of the warp-specialised shape, else all of the block's warps)
+    const int TILE = 32 * kShareCfg[k].ti, nw = kShareCfg[k].pw > 0 ? kShareCfg[k].pw : kShareCfg[k].nw;
     using R = ShareRecDB<DB>;
     if (nw > R::kMaxWarps) return;
     if (C % CS) return;
     const int S = C / CS, nblk = (D + DB - 1) / DB;
     const int AL = elem_align(dtype);
-    std::vector<int32_t> rec((size_t)nblk * S * R::kLen, 0), base((size_t)nblk * C);
+    std::vector<int32_t> rec((size_t)nblk * S * R::kLen, 0), base((size_t)2 * nblk * C);
     std::vector<int> npat((size_t)nblk * S);
     auto dl = [&](int dm, int ch) { return delays[(size_t)std::min(dm, D - 1) * C + ch]; };
     long long need = 0;
@@ -323,8 +325,12 @@ static void share_tables_db(const int32_t *delays, int D, int C, double foff, dd
                 }
                 const int b0 = lo - (lo % AL);
                 base[(size_t)b * C + s * CS + cc] = b0;
+                // elements of the row this block's trials read, a whole number of
+                // 16-byte units (<= rs, which rounds the largest up to 16 elements)
+                const long long nr = (long long)(hi - b0) + TILE;
+                base[(size_t)nblk * C + (size_t)b * C + s * CS + cc] = (int32_t)((nr + AL - 1) / AL * AL);
                 rowoff[cc] = dmin - b0;
-                need = std::max<long long>(need, (long long)(hi - b0) + TILE);
+                need = std::max<long long>(need, nr);
             }
             // patterns end to end in P; b_c without the row stride (added once rs is known)
             int poff = 0, rows = 0;
@@ -374,6 +380,7 @@ static void share_tables(const int32_t *delays, int D, int C, double foff, dd_dt
     switch (kShareCfg[k].dr * kShareCfg[k].nw) {
     case 32: share_tables_db<32>(delays, D, C, foff, dtype, k, T); break;
     case 48: share_tables_db<48>(delays, D, C, foff, dtype, k, T); break;
+    case 64: share_tables_db<64>(delays, D, C, foff, dtype, k, T); break;
     default: T = ShareTables(); break;
     }
 }
@@ -381,22 +388,28 @@ static void share_tables(const int32_t *delays, int D, int C, double foff, dd_dt
 static int build_share(const dd_plan *p, int k, ShareCfgData &c)
 {
     c = ShareCfgData();
+    if (!share_regs_ok(k)) return DD_OK;
     ShareTables T;
     share_tables(p->delays.data(), p->ndm, p->nchans, p->foff, p->dtype, k, T);
     if (!T.ok) return DD_OK;
     const size_t eb = in_elem_bytes(p->dtype);
-    // shared memory: input stages | records | 2 partial-sum buffers | mbarriers;
-    // the shape's target blocks per SM if it fits, else fewer (>= 2)
-    const int nis = kShareCfg[k].ns, minb = kShareCfg[k].minb;
+    // shared memory: input stages | records | partial-sum buffers | mbarriers;
+    // the shape's target blocks per SM if it fits, else fewer (>= 2).  The
+    // warp-specialised shape (one block per SM): pb slots of the block's trial
+    // offsets and a P buffer, and full/empty mbarriers per input stage and slot.
+    const ShareShape &sh = kShareCfg[k];
+    const int nis = sh.ns, minb = sh.minb;
     const int pm4 = (T.pmax + 3) / 4 * 4;
     const size_t rows_b = (size_t)nis * kShCS * T.rs * eb, rec_b = (size_t)nis * T.klen * 4;
-    const size_t bar_off = (rows_b + rec_b + (size_t)2 * pm4 * 4 + 15) / 16 * 16;
-    const size_t need_b = bar_off + nis * sizeof(uint64_t);
+    const size_t p_b = sh.pw > 0 ? (size_t)sh.pb * (sh.dr * sh.nw + pm4) * 4 : (size_t)2 * pm4 * 4;
+    const size_t bar_off = (rows_b + rec_b + p_b + 15) / 16 * 16;
+    const size_t nbar = sh.pw > 0 ? 2 * (size_t)(nis + sh.pb) : (size_t)nis;
+    const size_t need_b = bar_off + nbar * sizeof(uint64_t);
     bool fits = false;
     for (int nb = minb; nb >= std::min(minb, 2) && !fits; --nb)
         fits = need_b <= std::min<size_t>(p->smem_optin, (228 * 1024) / nb - 1024) - 1024;
     if (!fits) return DD_OK;
-    c.reach = (int64_t)*std::max_element(T.base.begin(), T.base.end()) + T.rs;
+    c.reach = (int64_t)*std::max_element(T.base.begin(), T.base.begin() + (size_t)T.nblk * p->nchans) + T.rs;
     c.nblk = T.nblk; c.nsub = T.nsub; c.rs = T.rs; c.pmax = pm4; c.bar_off = (int)bar_off;
     c.smem = need_b;
     cudaError_t e = cudaMalloc(&c.d_rec, T.rec.size() * 4);
@@ -553,8 +566,8 @@ int fast_configure(dd_plan *p)
     // default: the first available configuration in the order of measured
     // speed (kernel 5 shapes where their tables fit, then kernel 3, then
     // kernel 2); the autotuner may change it
-    static const int pref[] = {kShareBeg + 2, kShareBeg + 0, kShareBeg + 1, kNumFastCfg + 2, kNumFastCfg + 0,
-                               kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
+    static const int pref[] = {kShareBeg + 2, kShareBeg + 3, kShareBeg + 0, kShareBeg + 1, kNumFastCfg + 2,
+                               kNumFastCfg + 0, kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
     for (int k : pref)
         if (cfg_ok(f, k)) { f->active = k; break; }
     if (f->active < 0) { fast_release(p); return DD_OK; }   // tiled kernels unavailable
@@ -660,7 +673,7 @@ static int share_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitc
     a.in = in; a.pitch = pitch;
     a.nsamp_in_al = (p->nsamp_in + f->al - 1) / f->al * f->al;
     a.nchans = p->nchans; a.ndm = p->ndm; a.nsub = c.nsub; a.nout = p->nsamp_out;
-    a.rec = c.d_rec; a.base = c.d_base;
+    a.rec = c.d_rec; a.base = c.d_base; a.rlen = c.d_base + (size_t)c.nblk * p->nchans;
     a.rs = c.rs; a.pmax = c.pmax; a.bar_off = c.bar_off; a.nblk = c.nblk;
     a.ntile = tile_hi - tile_lo; a.t_base = tile_lo * tile;
     a.dgroup = std::max(1, std::min(dgroup, c.nblk));
@@ -809,8 +822,8 @@ int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStre
     // kernels 5, 3 and 2, each in its order of measured speed, so that a tie
     // keeps the earlier one (kernel 5's 48-trial shape first: fewest input
     // re-reads); kernel 4 (slower on every plan measured) runs only on request
-    static const int order[] = {kShareBeg + 2, kShareBeg + 0, kShareBeg + 1, kNumFastCfg + 2, kNumFastCfg + 0,
-                                kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
+    static const int order[] = {kShareBeg + 2, kShareBeg + 3, kShareBeg + 0, kShareBeg + 1, kNumFastCfg + 2,
+                                kNumFastCfg + 0, kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
     static_assert(sizeof(order) / sizeof(order[0]) == kNumAllCfg - kNumTmemCfg, "every timed configuration once");
     for (int k : order) {
         if (rc != DD_OK) break;
@@ -1100,7 +1113,7 @@ static int batch_enqueue(dd_batch *B, const void *const *ins, const int64_t *pit
                 sa.in = ins[i]; sa.pitch = pitches[i];
                 sa.nsamp_in_al = a.nsamp_in_al;
                 sa.nchans = p->nchans; sa.ndm = p->ndm; sa.nsub = sc.nsub; sa.nout = p->nsamp_out;
-                sa.rec = sc.d_rec; sa.base = sc.d_base;
+                sa.rec = sc.d_rec; sa.base = sc.d_base; sa.rlen = sc.d_base + (size_t)sc.nblk * p->nchans;
                 sa.rs = sc.rs; sa.pmax = sc.pmax; sa.bar_off = B->bar_off; sa.nblk = sc.nblk;
                 sa.ntile = a.ntile; sa.t_base = 0; sa.dgroup = a.dgroup;
                 sa.out = outs[i]; sa.partials = p->d_partials; sa.err = f->d_err; sa.smem = B->smem;

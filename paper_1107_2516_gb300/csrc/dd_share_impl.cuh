@@ -68,6 +68,7 @@ struct ShareLaunch {
     int64_t nout;
     const int32_t *rec;    // [nblk][nsub][kLen]
     const int32_t *base;   // [nblk][nchans] staged row start relative to the tile start (aligned)
+    const int32_t *rlen;   // [nblk][nchans] elements of that row the block's trials read (<= rs, aligned)
     int rs, pmax, bar_off, nblk;
     int64_t ntile;         // tiles of this launch, starting at output sample t_base
     int64_t t_base;
@@ -82,9 +83,10 @@ struct ShareLaunch {
 // warp w takes the contiguous rows the record assigns it (the host splits
 // the R rows evenly, w R / NW onwards), so a row's pattern (its fields) is
 // uniform in the warp and changes only at pattern ends, and lane l sums
-// element row_start + l of each of its rows: whole rows four at a time with
-// the pattern's offsets set up once, the pattern's partial last row alone.
-template <typename Tin, typename R, int CS, int NW>
+// element row_start + l of each of its rows: whole rows RPS at a time with
+// the pattern's offsets set up once (every load of a step issued before its
+// stores), the remaining rows one at a time.
+template <typename Tin, typename R, int CS, int NW, int RPS = 4>
 __device__ __forceinline__ void share_stage1(const int32_t *rec, const Tin *srow, float *Pb, int warp, int lane)
 {
     static_assert(NW <= R::kMaxWarps, "stage-1 split recorded for at most kMaxWarps warps");
@@ -107,14 +109,21 @@ __device__ __forceinline__ void share_stage1(const int32_t *rec, const Tin *srow
         int src[CS];                                                   // staged element of channel c at e0
 #pragma unroll
         for (int c = 0; c < CS; ++c) src[c] = b[1 + c] + e0;
-        for (; r + 4 <= rfull; r += 4) {
+        for (; r + RPS <= rfull; r += RPS) {
+            // all RPS x CS loads before the RPS stores: the staged rows and P
+            // are both shared memory, so the compiler may not move a store
+            // above a later load
+            float x[RPS][CS];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int o = (r + u) << 5;
-                float v = lane_ld<Tin>(srow + (src[0] + o));
+            for (int u = 0; u < RPS; ++u)
 #pragma unroll
-                for (int c = 1; c < CS; ++c) v += lane_ld<Tin>(srow + (src[c] + o));
-                Pb[e0 + o] = v;
+                for (int c = 0; c < CS; ++c) x[u][c] = lane_ld<Tin>(srow + (src[c] + ((r + u) << 5)));
+#pragma unroll
+            for (int u = 0; u < RPS; ++u) {
+                float v = x[u][0];
+#pragma unroll
+                for (int c = 1; c < CS; ++c) v += x[u][c];
+                Pb[e0 + ((r + u) << 5)] = v;
             }
         }
         for (; r < rend; ++r) {
@@ -224,17 +233,19 @@ __device__ __forceinline__ bool share_tile(const ShareLaunch &a, int blk, int64_
 
     // thread 0 issues subband s's copies with its rows' start offsets loaded
     // one subband earlier (the global loads' latency stays off the barrier path)
-    auto row_bytes = [&](int b, int64_t &g) -> uint32_t {
+    // each channel's row: the rl elements its DM trials read from column
+    // t0 + b on (fewer than rs near the top of the band), cut at the input's end
+    auto row_bytes = [&](int b, int rl, int64_t &g) -> uint32_t {
         g = t0 + b;
         int64_t n = a.nsamp_in_al - g;
-        n = n < 0 ? 0 : (n > rs ? rs : n);
+        n = n < 0 ? 0 : (n > rl ? rl : n);
         return (uint32_t)(n * (int64_t)sizeof(Tin));
     };
-    auto issue = [&](int s, const int (&rb)[CS]) {
+    auto issue = [&](int s, const int (&rb)[CS], const int (&rl)[CS]) {
         const int buf = (int)((g0 + s) % NS);
         uint32_t bytes = (uint32_t)(R::kLen * sizeof(int32_t));
 #pragma unroll
-        for (int cc = 0; cc < CS; ++cc) { int64_t g; bytes += row_bytes(rb[cc], g); }
+        for (int cc = 0; cc < CS; ++cc) { int64_t g; bytes += row_bytes(rb[cc], rl[cc], g); }
         mbar_arrive_tx(&bar[buf], bytes);
         bulk_g2s(srec + (size_t)buf * R::kLen, brec + (size_t)s * R::kLen, (uint32_t)(R::kLen * sizeof(int32_t)),
                  &bar[buf]);
@@ -242,16 +253,17 @@ __device__ __forceinline__ bool share_tile(const ShareLaunch &a, int blk, int64_
 #pragma unroll
         for (int cc = 0; cc < CS; ++cc) {
             int64_t g;
-            const uint32_t nb = row_bytes(rb[cc], g);
+            const uint32_t nb = row_bytes(rb[cc], rl[cc], g);
             if (nb)
                 bulk_g2s_hint(rows + (size_t)buf * stage_elems + (size_t)cc * rs,
                               in + (size_t)(s * CS + cc) * a.pitch + g, nb, &bar[buf], pol);
         }
     };
-    int rb[CS];
+    const int32_t *blen = a.rlen + (size_t)blk * a.nchans;
+    int rb[CS], rl[CS];
     auto load_rb = [&](int s) {
 #pragma unroll
-        for (int cc = 0; cc < CS; ++cc) rb[cc] = bbase[s * CS + cc];
+        for (int cc = 0; cc < CS; ++cc) { rb[cc] = bbase[s * CS + cc]; rl[cc] = blen[s * CS + cc]; }
     };
 
     float acc[DR][TI];
@@ -261,7 +273,7 @@ __device__ __forceinline__ bool share_tile(const ShareLaunch &a, int blk, int64_
         for (int i = 0; i < TI; ++i) acc[j][i] = 0.f;
 
     if (tid == 0) {
-        for (int s = 0; s < NS - 1 && s < nsub; ++s) { load_rb(s); issue(s, rb); }
+        for (int s = 0; s < NS - 1 && s < nsub; ++s) { load_rb(s); issue(s, rb, rl); }
         if (NS - 1 < nsub) load_rb(NS - 1);
     }
 
@@ -269,7 +281,7 @@ __device__ __forceinline__ bool share_tile(const ShareLaunch &a, int blk, int64_
     int q[DR];
     for (int s = 0; s < nsub; ++s) {
         if (tid == 0 && s + NS - 1 < nsub) {
-            issue(s + NS - 1, rb);
+            issue(s + NS - 1, rb, rl);
             if (s + NS < nsub) load_rb(s + NS);
         }
         const int buf = (int)((g0 + s) % NS);
@@ -383,18 +395,280 @@ __global__ void __launch_bounds__(NW * 32, MINB) mixed_batch_kernel(LaneBatchLau
     }
 }
 
+// Arrive on an mbarrier (no transaction bytes); release semantics at CTA scope.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Partial statistics of warps [gw0, gw0 + ngw) of the block (the accumulator
+// warps of the warp-specialised kernel; the others have left): the same
+// combination as block_stat_f32 / block_stat_i over those warps only, joined
+// by named barrier 1.  Every thread of those warps calls it; the group's
+// first thread writes record `lin`.
+template <bool kInt>
+__device__ __forceinline__ void group_stat_flush(const ShareLaunch &a, const ShareStat<kInt> &st, int64_t lin,
+                                                 int gw0, int ngw)
+{
+    __shared__ double gn[32], gm[32], gq[32];
+    __shared__ long long gs[32], gc[32];
+    __shared__ unsigned long long gu[32];
+    const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) - gw0;
+    if constexpr (kInt) {
+        long long n = st.n, s = st.s;
+        unsigned long long q = st.q;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            n += __shfl_xor_sync(0xffffffffu, n, off);
+            s += __shfl_xor_sync(0xffffffffu, s, off);
+            q += __shfl_xor_sync(0xffffffffu, q, off);
+        }
+        if (lane == 0) { gc[w] = n; gs[w] = s; gu[w] = q; }
+    } else {
+        int nw = st.n;
+        float sw = st.s;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            nw += __shfl_xor_sync(0xffffffffu, nw, off);
+            sw += __shfl_xor_sync(0xffffffffu, sw, off);
+        }
+        const float mw = nw ? sw / (float)nw : 0.f;
+        const float mt = st.n ? st.s / (float)st.n : 0.f;
+        const float d = mt - mw;
+        float qw = st.q + (float)st.n * d * d;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) qw += __shfl_xor_sync(0xffffffffu, qw, off);
+        if (lane == 0) { gn[w] = nw; gm[w] = mw; gq[w] = qw; }
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(ngw * 32) : "memory");
+    if (w == 0 && lane == 0) {
+        if constexpr (kInt) {
+            long long N = 0, S = 0;
+            unsigned long long Q = 0;
+            for (int v = 0; v < ngw; ++v) { N += gc[v]; S += gs[v]; Q += gu[v]; }
+            StatI *dst = reinterpret_cast<StatI *>(a.partials) + lin;
+            dst->n = N; dst->sum = S; dst->sumsq = Q;
+        } else {
+            double N = 0, S = 0;
+            for (int v = 0; v < ngw; ++v) { N += gn[v]; S += gn[v] * (double)gm[v]; }
+            const double M = N > 0 ? S / N : 0.0;
+            double Q = 0;
+            for (int v = 0; v < ngw; ++v) {
+                const double e = (double)gm[v] - M;
+                Q += (double)gq[v] + gn[v] * e * e;
+            }
+            StatF *dst = reinterpret_cast<StatF *>(a.partials) + lin;
+            dst->n = N; dst->mean = M; dst->m2 = Q;
+        }
+    }
+}
+
+// Registers of the warp-specialised block: a launch of T threads gets at
+// most 65536 / T per thread (a multiple of 8).  When that is below what the
+// stage-2 warps need (their DR x TI accumulators: kWsAccRegs), the stage-1
+// warps give registers back with setmaxnreg.dec and the stage-2 warps take
+// them with setmaxnreg.inc; the two shares together stay within the block's
+// launch allocation (checked on the host against the compiled register count
+// before the shape is used: an increase the block cannot cover would wait
+// forever).
+constexpr int kWsAccRegs = 168;
+template <int NW, int PW>
+struct WsRegs {
+    static constexpr int kThreads = (NW + PW) * 32;
+    static constexpr int kLaunch = (65536 / kThreads) / 8 * 8 > 255 ? 248 : (65536 / kThreads) / 8 * 8;
+    static constexpr bool kSplit = kLaunch < kWsAccRegs;
+    // stage-1 warps' share: what the launch leaves after the stage-2 warps' 168,
+    // 8 registers short of the most that would fit (slack for the compiled count)
+    static constexpr int kProd = kSplit ? ((NW + PW) * kLaunch - NW * kWsAccRegs) / PW / 8 * 8 - 8 : kLaunch;
+    static_assert(!kSplit || (kProd >= 24 && kProd % 8 == 0), "stage-1 warps need at least 24 registers");
+    static_assert(!kSplit || (PW % 4 == 0 && NW % 4 == 0), "setmaxnreg acts on whole warpgroups");
+    // the compiled register count per thread the split needs
+    static constexpr int kNeed = kSplit ? (PW * kProd + NW * kWsAccRegs + NW + PW - 1) / (NW + PW) : 0;
+};
+
+// Kernel 5, warp-specialised: the same two stages on separate warps.  Warps
+// [0, PW) form subband s's partial sums (stage 1) into P slot s % PB and copy
+// the block's trial offsets next to them; warps [PW, PW + NW) add slot s into
+// their trials' accumulators (stage 2).  Hand-offs are mbarriers, not a block
+// barrier per subband:
+//   full[i]   input stage i has landed (TMA transaction bytes),
+//   empty[i]  every stage-1 warp is done with input stage i,
+//   pfull[b]  every stage-1 warp has written slot b,
+//   pempty[b] every stage-2 warp has read slot b,
+// so stage 1 runs up to PB - 1 subbands ahead of stage 2 and the two keep the
+// shared-memory pipe busy together.  Lane 0 of warp 0 issues the input copies
+// NS - 1 subbands ahead: at the top of subband s, those of subband s + NS - 1
+// into the stage subband s - 1 used, once every stage-1 warp is done with it.
+// One block per SM: NW * DR trials x 32 * TI samples of accumulators take
+// most of the register file, the stage-1 warps the rest.
+// Every wait is bounded; a warp whose wait gives up stops, the others then
+// give up on theirs, and the issuing thread waits (bounded) for its copies
+// still in flight before it returns.
+template <typename Tin, bool kInt, int TI, int DR, int NW, int PW, int CS, int NPMAX, int NS, int PB>
+__global__ void __launch_bounds__((NW + PW) * 32, 1) share_ws_kernel(ShareLaunch a)
+{
+    using Regs = WsRegs<NW, PW>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int kDmBlk = DR * NW;
+    using R = ShareRec<CS, NPMAX, kDmBlk>;
+    static_assert(NS >= 2 && PB >= 2, "input ring and slot ring need two entries");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rs = a.rs, nsub = a.nsub;
+
+    // layout: [NS][CS][rs] Tin rows | [NS][kLen] int32 records |
+    //         [PB] slots {int32 q[kDmBlk], float P[pmax]} | mbarriers at bar_off
+    const size_t stage_elems = (size_t)CS * rs;
+    Tin *rows = reinterpret_cast<Tin *>(smem);
+    int32_t *srec = reinterpret_cast<int32_t *>(smem + NS * stage_elems * sizeof(Tin));
+    int32_t *slots = srec + NS * R::kLen;
+    const size_t slot_len = (size_t)kDmBlk + a.pmax;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + a.bar_off);
+    uint64_t *empty = full + NS, *pfull = full + 2 * NS, *pempty = full + 2 * NS + PB;
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], PW); }
+        for (int b = 0; b < PB; ++b) { mbar_init(&pfull[b], PW); mbar_init(&pempty[b], NW); }
+        mbar_fence_init();
+    }
+    __syncthreads();
+    int blk;
+    int64_t t0;
+    {
+        LaneLaunch r{};
+        r.dgroup = a.dgroup; r.ntile = a.ntile; r.nblk = a.nblk;
+        lane_raster<TI>(r, blockIdx.x, blk, t0);
+        t0 += a.t_base;
+    }
+
+    if (warp < PW) {
+        // ---- stage 1 (and the input copies)
+        if constexpr (Regs::kSplit) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(Regs::kProd));
+        const Tin *__restrict__ in = static_cast<const Tin *>(a.in);
+        const int32_t *brec = a.rec + (size_t)blk * nsub * R::kLen;
+        const int32_t *bbase = a.base + (size_t)blk * a.nchans;
+        const int32_t *blen = a.rlen + (size_t)blk * a.nchans;
+        auto row_bytes = [&](int b, int rl, int64_t &g) -> uint32_t {
+            g = t0 + b;
+            int64_t n = a.nsamp_in_al - g;
+            n = n < 0 ? 0 : (n > rl ? rl : n);
+            return (uint32_t)(n * (int64_t)sizeof(Tin));
+        };
+        int rb[CS], rl[CS];
+        auto load_rb = [&](int s) {
+#pragma unroll
+            for (int cc = 0; cc < CS; ++cc) { rb[cc] = bbase[s * CS + cc]; rl[cc] = blen[s * CS + cc]; }
+        };
+        auto issue = [&](int s) {
+            const int buf = s % NS;
+            uint32_t bytes = (uint32_t)(R::kLen * sizeof(int32_t));
+#pragma unroll
+            for (int cc = 0; cc < CS; ++cc) { int64_t g; bytes += row_bytes(rb[cc], rl[cc], g); }
+            mbar_arrive_tx(&full[buf], bytes);
+            bulk_g2s(srec + (size_t)buf * R::kLen, brec + (size_t)s * R::kLen, (uint32_t)(R::kLen * sizeof(int32_t)),
+                     &full[buf]);
+            const uint64_t pol = l2_evict_last();
+#pragma unroll
+            for (int cc = 0; cc < CS; ++cc) {
+                int64_t g;
+                const uint32_t nb = row_bytes(rb[cc], rl[cc], g);
+                if (nb)
+                    bulk_g2s_hint(rows + (size_t)buf * stage_elems + (size_t)cc * rs,
+                                  in + (size_t)(s * CS + cc) * a.pitch + g, nb, &full[buf], pol);
+            }
+        };
+        int issued = 0;   // copies issued (thread 0)
+        if (tid == 0) {
+            for (; issued < NS - 1 && issued < nsub; ++issued) { load_rb(issued); issue(issued); }
+            if (issued < nsub) load_rb(issued);
+        }
+        bool ok = true;
+        int s = 0;
+        for (; s < nsub; ++s) {
+            if (warp == 0) {
+                // refill the stage subband s - 1 used once every stage-1 warp is done with it
+                bool go = true;
+                if (lane == 0 && issued < nsub) {
+                    if (s >= 1) go = mbar_wait(&empty[(s - 1) % NS], (uint32_t)(((s - 1) / NS) & 1), a.err);
+                    if (go) {
+                        issue(issued);
+                        ++issued;
+                        if (issued < nsub) load_rb(issued);
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, go ? 1 : 0, 0) != 0;
+            }
+            const int pb = s % PB, ib = s % NS;
+            if (ok && s >= PB) ok = mbar_wait(&pempty[pb], (uint32_t)(((s / PB) - 1) & 1), a.err);
+            if (ok) ok = mbar_wait(&full[ib], (uint32_t)((s / NS) & 1), a.err);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            const int32_t *rec = srec + (size_t)ib * R::kLen;
+            int32_t *slot = slots + (size_t)pb * slot_len;
+            share_stage1<Tin, R, CS, PW, 8>(rec, rows + (size_t)ib * stage_elems,
+                                            reinterpret_cast<float *>(slot + kDmBlk), warp, lane);
+            if (warp == PW - 1)
+                for (int j = lane; j < kDmBlk; j += 32) slot[j] = rec[R::kTrial + j];
+            __syncwarp();
+            if (lane == 0) { mbar_arrive(&pfull[pb]); mbar_arrive(&empty[ib]); }
+        }
+        // after a wait gave up: let the copies still in flight land before leaving
+        if (tid == 0)
+            for (int u = s; u < issued; ++u) mbar_wait(&full[u % NS], (uint32_t)((u / NS) & 1), a.err);
+        return;
+    }
+
+    // ---- stage 2: one shared word per add
+    if constexpr (Regs::kSplit) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kWsAccRegs));
+    const int cw = warp - PW;
+    float acc[DR][TI];
+#pragma unroll
+    for (int j = 0; j < DR; ++j)
+#pragma unroll
+        for (int i = 0; i < TI; ++i) acc[j][i] = 0.f;
+    bool ok = true;
+    for (int s = 0; s < nsub; ++s) {
+        const int pb = s % PB;
+        ok = __all_sync(0xffffffffu, mbar_wait(&pfull[pb], (uint32_t)((s / PB) & 1), a.err));
+        if (!ok) break;
+        const int32_t *slot = slots + (size_t)pb * slot_len;
+        const float *Pb = reinterpret_cast<const float *>(slot + kDmBlk);
+        int q[DR];
+#pragma unroll
+        for (int j = 0; j < DR; j += 4) {
+            const int4 v = *reinterpret_cast<const int4 *>(slot + cw * DR + j);
+            q[j] = v.x; q[j + 1] = v.y; q[j + 2] = v.z; q[j + 3] = v.w;
+        }
+#pragma unroll
+        for (int j = 0; j < DR; ++j) {
+            const float *pp = Pb + q[j] + lane;
+#pragma unroll
+            for (int i = 0; i < TI; ++i) acc[j][i] += pp[32 * i];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&pempty[pb]);
+    }
+    ShareStat<kInt> st;
+    if (ok) share_store<kInt, TI, DR>(a, acc, blk * kDmBlk + cw * DR, t0, lane, st);
+    group_stat_flush<kInt>(a, st, blockIdx.x, PW, NW);
+}
+
 // Compiled shapes: subbands of 4 channels, at most 16 patterns per (block,
-// subband); {samples per lane, DM trials per warp, warps, resident blocks per
-// SM the register budget targets, input stages}.
+// subband); {samples per lane, DM trials per warp, warps (stage-2 warps in
+// the warp-specialised form), resident blocks per SM the register budget
+// targets, input stages, stage-1 warps (0: the one-barrier-per-subband
+// kernel, whose warps do both stages), partial-sum slots}.
 constexpr int kShCS = 4, kShNP = 16;
-struct ShareShape { int ti, dr, nw, minb, ns; };
-constexpr int kNumShareCfg = 3;
-constexpr ShareShape kShareCfg[kNumShareCfg] = {{16, 8, 4, 3, 2}, {8, 8, 4, 5, 2}, {16, 8, 6, 2, 2}};
+struct ShareShape { int ti, dr, nw, minb, ns, pw, pb; };
+constexpr int kNumShareCfg = 4;
+constexpr ShareShape kShareCfg[kNumShareCfg] = {
+    {16, 8, 4, 3, 2, 0, 2}, {8, 8, 4, 5, 2, 0, 2}, {16, 8, 6, 2, 2, 0, 2}, {16, 8, 8, 1, 3, 8, 3}};
 template <int DB>
 using ShareRecDB = ShareRec<kShCS, kShNP, DB>;
 
 cudaError_t share_launch(int k, dd_dtype t, const ShareLaunch &a, cudaStream_t s);
 cudaError_t share_prepare(int k, size_t optin);
+// false if shape k's kernels were compiled with fewer registers than its
+// register split needs (the shape is then not used)
+bool share_regs_ok(int k);
 // Mixed persistent batch of kernel 5 shape 0 and kernel 3 shape 2 (the same
 // block geometry): grid = sms * that shape's resident blocks per SM.
 cudaError_t mixed_batch_launch(const LaneBatchLaunch &b, int sms, size_t smem, cudaStream_t s);

@@ -378,7 +378,8 @@ def dd_server_ring_schedule(maxshift: int, chunk: int, seqs):
 def dd_share_tables(delays: np.ndarray, foff: float, dtype: int, config: int):
     """Kernel 5's tables (host only) for a delay table [ndm][nchans]: None if the
     shape cannot run it, else dict(rec [blocks][subbands][kLen], base
-    [blocks][nchans], rs, pmax, klen)."""
+    [blocks][nchans] staged row starts, rlen [blocks][nchans] staged row
+    lengths, rs, pmax, klen)."""
     d = np.ascontiguousarray(delays, dtype=np.int32)
     ndm, nch = d.shape
     info = np.zeros(6, np.int32)
@@ -388,10 +389,10 @@ def dd_share_tables(delays: np.ndarray, foff: float, dtype: int, config: int):
         return None
     nblk, nsub, rs, pmax, klen = (int(v) for v in info[1:])
     rec = np.empty((nblk, nsub, klen), np.int32)
-    base = np.empty((nblk, nch), np.int32)
+    base = np.empty((2, nblk, nch), np.int32)
     _check(load().dd_share_tables(_ptr(d), ndm, nch, float(foff), int(dtype), int(config), _ptr(info), _ptr(rec),
                                   rec.size, _ptr(base), base.size))
-    return {"rec": rec, "base": base, "rs": rs, "pmax": pmax, "klen": klen}
+    return {"rec": rec, "base": base[0], "rlen": base[1], "rs": rs, "pmax": pmax, "klen": klen}
 
 
 def dd_batch_beam_config(batch: int, beam: int) -> int:

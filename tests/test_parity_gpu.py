@@ -105,7 +105,7 @@ def test_small_workload_parity(dtype, kernel):
 
 @pytest.mark.parametrize("tile", [(0, 1), (0, 3), (1, 8), (1, 2), (2, 16), (3, 8), (3, 1), (4, 4),
                                   (5, 8), (5, 3), (6, 16), (6, 2), (7, 8), (7, 3), (8, 16), (8, 1),
-                                  (9, 8), (9, 1), (10, 4), (11, 8), (11, 1)])
+                                  (9, 8), (9, 1), (10, 4), (11, 8), (11, 1), (12, 8)])
 @pytest.mark.parametrize("dtype", ["f32", "u8", "f16"])
 def test_small_workload_tile_configs(dtype, tile):
     # every compiled tile configuration of kernels 2-4 and several raster
@@ -119,7 +119,7 @@ def test_small_workload_tile_configs(dtype, tile):
         # kernel 4 windows must fit the warp's TMEM buffer (config 8 does not
         # at this plan's ~25 samples per DM step); kernel 5 needs at most 16
         # delay patterns per block and 4-channel subband (this plan has 29)
-        assert tile[0] in (8, 9, 10, 11) and e.code == 1
+        assert tile[0] in (8, 9, 10, 11, 12) and e.code == 1
         pytest.skip("configuration unavailable for this plan")
     assert used == (2 if tile[0] < 3 else 3 if tile[0] < 7 else 4 if tile[0] < 9 else 5)
 
@@ -143,11 +143,11 @@ def test_kernel4_lofar_geometry(dtype, tile):
     assert used == 4
 
 
-@pytest.mark.parametrize("tile", [(9, 8), (9, 1), (10, 16), (11, 8), (11, 1)])
+@pytest.mark.parametrize("tile", [(9, 8), (9, 1), (10, 16), (11, 8), (11, 1), (12, 8), (12, 1), (12, 64)])
 @pytest.mark.parametrize("dtype", ["f32", "u8", "f16"])
 def test_kernel5_lofar_full_band(dtype, tile):
     # the shared-subband kernel on the full LOFAR band (1024 channels: at most
-    # 8 delay patterns per block of 32 or 48 trials and 4-channel subband), 100
+    # 10 delay patterns per block of 32, 48 or 64 trials and 4-channel subband), 100
     # trials (ragged last block), 2^15 samples, two pulses
     lw = synth.workload("lofar_f32")
     dms = [0.05 * i for i in range(100)]
@@ -185,7 +185,7 @@ def test_autotune_keeps_parity():
     out = torch.empty(wl.ndm * plan.nsamp_out, dtype=torch.float32, device="cuda")
     plan.autotune(x, wl.nsamp, out)
     cfg, group, tr, nw = plan.tile
-    assert cfg in (0, 1, 2, 3, 4, 5, 6, 9, 10, 11) and group in (4, 8, 16, 64) and tr in (8, 16, 20, 28, 36) \
+    assert cfg in (0, 1, 2, 3, 4, 5, 6, 9, 10, 11, 12) and group in (4, 8, 16, 64) and tr in (8, 16, 20, 28, 36) \
         and nw in (4, 6, 8, 12)
     plan.execute(x, wl.nsamp, out)
     torch.cuda.synchronize()
@@ -224,7 +224,7 @@ def test_edge_shapes(case, dtype):
     _, m = oracle.delays(nch, fch1, foff, tsamp, dms)
     nsamp = m + extra
     d_o, _ = oracle.delays(nch, fch1, foff, tsamp, dms)
-    k5_tables = any(ddc.dd_share_tables(np.asarray(d_o), foff, DTYPES[dtype], c) is not None for c in (9, 10, 11))
+    k5_tables = any(ddc.dd_share_tables(np.asarray(d_o), foff, DTYPES[dtype], c) is not None for c in range(9, 13))
     al = 4 if dtype == "f32" else 16
     # the shape's own pitch (often not 16-byte aligned: the tiled kernels then
     # fall back to kernel 1) and the next aligned one (the tiled kernels run)
@@ -315,7 +315,7 @@ def test_process_host_matches_device_path():
     plan.close()
 
 
-@pytest.mark.parametrize("kernel,tile", [(3, (5, 8)), (3, (6, 1)), (5, (9, 4)), (5, (11, 16))])
+@pytest.mark.parametrize("kernel,tile", [(3, (5, 8)), (3, (6, 1)), (5, (9, 4)), (5, (11, 16)), (5, (12, 64))])
 @pytest.mark.parametrize("dtype", ["f32", "u8"])
 def test_process_host_pipelined(dtype, kernel, tile):
     # dd_process_host with kernels 3 and 5 copies the input in 8 column chunks

@@ -6,8 +6,8 @@ addresses.
 Stage 1: for subband s of DM block b and the time tile at t0, P[e] (e < E)
 sums the subband's 4 staged input rows at the staged element b_c + e of the
 pattern e belongs to; the rows hold input columns t0 + base[b][c] onwards,
-as many as the input has (the rest of a staged row is never written: NaN
-here).  Stage 2: trial j adds P[q_j + i] to its output sample t0 + i."""
+rlen[b][c] of them or as many as the input has (the rest of a staged row is
+never written: NaN here).  Stage 2: trial j adds P[q_j + i] to its output sample t0 + i."""
 import numpy as np
 import pytest
 
@@ -19,7 +19,9 @@ from paper_1107_2516_gb300 import dd as ddc
 
 CS = 4
 NPMAX, MAXW = 16, 8          # pattern slots per record; warps the stage-1 split records
-SHAPES = {9: (512, 32), 10: (256, 32), 11: (512, 48)}     # config: (tile, trials per block)
+SHAPES = {9: (512, 32), 10: (256, 32), 11: (512, 48), 12: (512, 64)}     # config: (tile, trials per block)
+# warps the stage-1 rows are split over (config 12: its 8 stage-1 warps)
+SPLIT = {9: 4, 10: 4, 11: 6, 12: 8}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -33,7 +35,9 @@ def emulate(x, nsamp, d, foff, dtype, config):
     t = ddc.dd_share_tables(d, foff, dtype, config)
     if t is None:
         return None
-    rec, base, rs = t["rec"], t["base"], t["rs"]
+    rec, base, rlen, rs = t["rec"], t["base"], t["rlen"], t["rs"]
+    al_el = 16 if dtype == dd.DD_U8 else 8 if dtype == dd.DD_F16 else 4
+    assert np.all(rlen <= rs) and np.all(rlen % al_el == 0) and np.all(rlen > 0)
     tile, db = SHAPES[config]
     ndm, nch = d.shape
     nblk, nsub, _ = rec.shape
@@ -49,8 +53,9 @@ def emulate(x, nsamp, d, foff, dtype, config):
             for s in range(nsub):
                 stage = np.full(CS * rs, np.nan)
                 for c in range(CS):
+                    # the kernel copies the channel's own row length (its trials' reach), not rs
                     g = t0 + int(base[b, s * CS + c])
-                    n = max(0, min(rs, nsamp_al - g))
+                    n = max(0, min(int(rlen[b, s * CS + c]), nsamp_al - g))
                     stage[c * rs:c * rs + n] = x[s * CS + c, g:g + n]
                 r = rec[b, s]
                 E = int(r[db])
@@ -77,10 +82,11 @@ CASES = [
     (128, 150.0, -0.0234375, 163.84e-6, [0.1 * i for i in range(60)], 2700, "f32"),       # 11-15 patterns
     (96, 150.0 - 95 * 0.0234375, 0.0234375, 163.84e-6, [0.1 * i for i in range(50)], 2300, "u8"),  # ascending
     (256, 150.0, -0.046875, 163.84e-6, [0.05 * i for i in range(100)], 3000, "f32"),      # 13 / 17 patterns
+    (128, 150.0, -0.0234375, 163.84e-6, [0.05 * i for i in range(100)], 2900, "f32"),     # every shape (64 + 36 trials)
 ]
 
 
-@pytest.mark.parametrize("config", [9, 10, 11])
+@pytest.mark.parametrize("config", [9, 10, 11, 12])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_kernel5_tables_reproduce_brute_force(case, config):
     nch, fch1, foff, ts, dms, nsamp, dt = CASES[case]
@@ -149,7 +155,7 @@ def _stage1_rows(rec_row, db, nw):
     return cover
 
 
-@pytest.mark.parametrize("config", [9, 10, 11])
+@pytest.mark.parametrize("config", [9, 10, 11, 12])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_stage1_rows_cover_every_sum_once(case, config):
     nch, fch1, foff, ts, dms, nsamp, dt = CASES[case]
@@ -158,7 +164,7 @@ def test_stage1_rows_cover_every_sum_once(case, config):
     if t is None:
         pytest.skip("shape unavailable for this plan")
     _, db = SHAPES[config]
-    nw = {9: 4, 10: 4, 11: 6}[config]
+    nw = SPLIT[config]
     rec = t["rec"]
     for b in range(rec.shape[0]):
         for s in range(rec.shape[1]):
@@ -166,10 +172,11 @@ def test_stage1_rows_cover_every_sum_once(case, config):
 
 
 def test_stage1_rows_cover_every_sum_once_lofar():
-    # the benchmark plan's tables (every block, every 16th subband), configs 9 and 11
+    # the benchmark plan's tables (every block, every 16th subband), configs 9, 11 and 12
     wl = synth.workload("lofar_f32")
     d, _ = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
-    for config, nw in ((9, 4), (11, 6)):
+    for config in (9, 11, 12):
+        nw = SPLIT[config]
         t = ddc.dd_share_tables(np.asarray(d), wl.foff, dd.DD_F32, config)
         assert t is not None
         _, db = SHAPES[config]
