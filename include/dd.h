@@ -180,7 +180,7 @@ DD_API int dd_process_host(dd_plan *plan, const void *in_host, int64_t in_pitch,
                     void *stream);
 
 /* Select the de-dispersion kernel for a plan: 0 = automatic (default: the
- * first available of tile configurations 11, 12, 9, 10, 5, 3, 6, 4, 1, 0, 2 —
+ * first available of tile configurations 12, 11, 9, 10, 5, 3, 6, 4, 1, 0, 2 —
  * kernel 5 shapes where their tables fit the plan, then kernel 3 and kernel 2
  * shapes, in the order of measured speed — or the autotuner's choice;
  * kernel 1 if no tiled configuration fits),

@@ -352,8 +352,16 @@ static void share_tables_db(const int32_t *delays, int D, int C, double foff, dd
                 rows += (W + 31) / 32;
             }
             prow[pats.size()] = rows;
-            // stage-1 split: warp w's first row and the pattern holding it
-            for (int w = 0; w <= nw; ++w) t[R::kWarp + w] = (int)((long long)w * rows / nw);
+            // stage-1 split: warp w's first row and the pattern holding it.
+            // Warp 0 (whose first thread issues the input copies and waits
+            // while the copy engine takes them) gets kShareCfg[k].w0 percent
+            // of another warp's share of the rows, the others equal shares.
+            {
+                const long long w0 = kShareCfg[k].w0, tot = w0 + 100LL * (nw - 1);
+                t[R::kWarp] = 0;
+                for (int w = 1; w <= nw; ++w)
+                    t[R::kWarp + w] = (int)(((long long)rows * (w0 + 100LL * (w - 1)) + tot / 2) / tot);
+            }
             for (int w = 0; w < nw; ++w) {
                 const int r0 = t[R::kWarp + w];
                 int q = 0;
@@ -566,7 +574,7 @@ int fast_configure(dd_plan *p)
     // default: the first available configuration in the order of measured
     // speed (kernel 5 shapes where their tables fit, then kernel 3, then
     // kernel 2); the autotuner may change it
-    static const int pref[] = {kShareBeg + 2, kShareBeg + 3, kShareBeg + 0, kShareBeg + 1, kNumFastCfg + 2,
+    static const int pref[] = {kShareBeg + 3, kShareBeg + 2, kShareBeg + 0, kShareBeg + 1, kNumFastCfg + 2,
                                kNumFastCfg + 0, kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
     for (int k : pref)
         if (cfg_ok(f, k)) { f->active = k; break; }
@@ -820,9 +828,9 @@ int fast_autotune(dd_plan *p, const void *in, int64_t pitch, void *out, cudaStre
     // tile's blocks together)
     const int groups[] = {64, 16, 8, 4};
     // kernels 5, 3 and 2, each in its order of measured speed, so that a tie
-    // keeps the earlier one (kernel 5's 48-trial shape first: fewest input
+    // keeps the earlier one (kernel 5's warp-specialised 64-trial shape first, then the 48-trial one: fewest input
     // re-reads); kernel 4 (slower on every plan measured) runs only on request
-    static const int order[] = {kShareBeg + 2, kShareBeg + 3, kShareBeg + 0, kShareBeg + 1, kNumFastCfg + 2,
+    static const int order[] = {kShareBeg + 3, kShareBeg + 2, kShareBeg + 0, kShareBeg + 1, kNumFastCfg + 2,
                                 kNumFastCfg + 0, kNumFastCfg + 3, kNumFastCfg + 1, 1, 0, 2};
     static_assert(sizeof(order) / sizeof(order[0]) == kNumAllCfg - kNumTmemCfg, "every timed configuration once");
     for (int k : order) {

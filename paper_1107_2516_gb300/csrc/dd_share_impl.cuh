@@ -81,7 +81,7 @@ struct ShareLaunch {
 // Stage 1 of one subband: P[e] for e < E (the patterns' sums end to end).
 // Each pattern's sums form rows of 32 consecutive e (the last one partial);
 // warp w takes the contiguous rows the record assigns it (the host splits
-// the R rows evenly, w R / NW onwards), so a row's pattern (its fields) is
+// the R rows in order, warp 0 a smaller share), so a row's pattern (its fields) is
 // uniform in the warp and changes only at pattern ends, and lane l sums
 // element row_start + l of each of its rows: whole rows RPS at a time with
 // the pattern's offsets set up once (every load of a step issued before its
@@ -655,12 +655,15 @@ __global__ void __launch_bounds__((NW + PW) * 32, 1) share_ws_kernel(ShareLaunch
 // subband); {samples per lane, DM trials per warp, warps (stage-2 warps in
 // the warp-specialised form), resident blocks per SM the register budget
 // targets, input stages, stage-1 warps (0: the one-barrier-per-subband
-// kernel, whose warps do both stages), partial-sum slots}.
+// kernel, whose warps do both stages), partial-sum slots, stage-1 rows of
+// warp 0 in percent of another warp's (its first thread issues the input
+// copies, which hold it for ~1000 cycles per subband: a smaller share keeps
+// it from being the last one at each subband's barrier or hand-off)}.
 constexpr int kShCS = 4, kShNP = 16;
-struct ShareShape { int ti, dr, nw, minb, ns, pw, pb; };
+struct ShareShape { int ti, dr, nw, minb, ns, pw, pb, w0; };
 constexpr int kNumShareCfg = 4;
 constexpr ShareShape kShareCfg[kNumShareCfg] = {
-    {16, 8, 4, 3, 2, 0, 2}, {8, 8, 4, 5, 2, 0, 2}, {16, 8, 6, 2, 2, 0, 2}, {16, 8, 8, 1, 3, 8, 3}};
+    {16, 8, 4, 3, 2, 0, 2, 70}, {8, 8, 4, 5, 2, 0, 2, 70}, {16, 8, 6, 2, 2, 0, 2, 70}, {16, 8, 8, 1, 3, 8, 3, 50}};
 template <int DB>
 using ShareRecDB = ShareRec<kShCS, kShNP, DB>;
 

@@ -92,10 +92,10 @@ def test_sampled_points(lofar, capsys):
               f"outputs): max|err| {worst:.3g} (bound {fp_tol(WL.nchans):.3g})")
 
 
-@pytest.mark.parametrize("cfg", [7, 8, 9, 11])
+@pytest.mark.parametrize("cfg", [7, 8, 9, 11, 12])
 def test_kernel4_full_size(lofar, cfg):
     # the tensor-memory kernel (configs 7, 8) and the shared-subband kernel
-    # (configs 9, 11) on the full plan: sampled points and one whole row
+    # (configs 9, 11, 12) on the full plan: sampled points and one whole row
     x, d, nout = lofar["x"], lofar["d"], lofar["nout"]
     wl = WL
     plan = dd.Plan(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list, wl.widths, wl.sigma,

@@ -20,8 +20,10 @@ from paper_1107_2516_gb300 import dd as ddc
 CS = 4
 NPMAX, MAXW = 16, 8          # pattern slots per record; warps the stage-1 split records
 SHAPES = {9: (512, 32), 10: (256, 32), 11: (512, 48), 12: (512, 64)}     # config: (tile, trials per block)
-# warps the stage-1 rows are split over (config 12: its 8 stage-1 warps)
+# warps the stage-1 rows are split over (config 12: its 8 stage-1 warps), and
+# warp 0's share in percent of another warp's (it also issues the copies)
 SPLIT = {9: 4, 10: 4, 11: 6, 12: 8}
+W0 = {9: 70, 10: 70, 11: 70, 12: 50}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -123,10 +125,18 @@ def test_kernel5_tables_bad_config():
         ddc.dd_share_tables(d, -1.0, dd.DD_F32, 5)
 
 
-def _stage1_rows(rec_row, db, nw):
+def _split(R, nw, w0):
+    """Row boundaries b_0 .. b_nw: warp 0 weighs w0 (percent), the others 100,
+    boundaries rounded half up in integers."""
+    tot = w0 + 100 * (nw - 1)
+    return [0] + [(R * (w0 + 100 * (w - 1)) + tot // 2) // tot for w in range(1, nw + 1)]
+
+
+def _stage1_rows(rec_row, db, nw, w0):
     """Kernel 5's stage-1 work split, restated: the patterns' sums (index space
     e < E) cut into rows of 32 inside each pattern; warp w of nw takes rows
-    [w R / nw, (w+1) R / nw) and lane l element row_start + l of each.  The
+    [b_w, b_w+1) (_split: warp 0 a w0-percent share) and lane l element
+    row_start + l of each.  The
     record's per-pattern start / rows-before fields and per-warp first row and
     pattern must be exactly these.  Returns how often each e is summed."""
     E = int(rec_row[db])
@@ -141,8 +151,10 @@ def _stage1_rows(rec_row, db, nw):
     R = int(incl[-1])
     wt = rec_row[db + 4 + NPMAX * 8:].astype(np.int64)
     cover = np.zeros(E, np.int64)
+    bnd = _split(R, nw, w0)
+    assert bnd[-1] == R and all(bnd[i] <= bnd[i + 1] for i in range(nw))
     for w in range(nw):
-        r0, r1 = w * R // nw, (w + 1) * R // nw
+        r0, r1 = bnd[w], bnd[w + 1]
         assert wt[w] == r0 and wt[w + 1] == r1
         if r0 < r1:
             assert wt[MAXW + 1 + w] == int(np.searchsorted(incl, r0, side="right"))
@@ -168,7 +180,7 @@ def test_stage1_rows_cover_every_sum_once(case, config):
     rec = t["rec"]
     for b in range(rec.shape[0]):
         for s in range(rec.shape[1]):
-            assert np.all(_stage1_rows(rec[b, s], db, nw) == 1), (b, s)
+            assert np.all(_stage1_rows(rec[b, s], db, nw, W0[config]) == 1), (b, s)
 
 
 def test_stage1_rows_cover_every_sum_once_lofar():
@@ -183,5 +195,5 @@ def test_stage1_rows_cover_every_sum_once_lofar():
         rec = t["rec"]
         for b in range(rec.shape[0]):
             for s in range(0, rec.shape[1], 16):
-                assert np.all(_stage1_rows(rec[b, s], db, nw) == 1), (config, b, s)
+                assert np.all(_stage1_rows(rec[b, s], db, nw, W0[config]) == 1), (config, b, s)
 
