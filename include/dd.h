@@ -325,12 +325,14 @@ DD_API int dd_batch_info(const dd_batch *batch, int32_t *config, int64_t *nitems
 DD_API int dd_batch_set_launch_mode(dd_batch *batch, int32_t per_beam);
 DD_API int dd_batch_launch_mode(const dd_batch *batch, int32_t *per_beam);
 
-/* Tile configuration beam `beam` runs in the batch (9 or 5 under the mixed
- * configuration 9, else the batch's), -1 if it runs the generic kernel by
- * its own launch.  A plan set to that configuration alone (dd_plan_set_tile)
- * reproduces the beam's batched output bit for bit.  In the per-beam launch
- * mode every beam with kernel 5 tables runs kernel 5; in the persistent grid
- * only those whose tables fit three blocks per SM. */
+/* Tile configuration beam `beam` runs in the batch (a kernel 5 shape or 5
+ * under the mixed configuration 9, else the batch's), -1 if it runs the
+ * generic kernel by its own launch.  A plan set to that configuration alone
+ * (dd_plan_set_tile) reproduces the beam's batched output bit for bit.  In
+ * the per-beam launch mode every beam with kernel 5 tables runs its first
+ * available kernel 5 shape of 12, 11, 9, 10 (the order a plan starts from);
+ * in the persistent grid shape 9, for the beams whose tables fit three
+ * blocks per SM. */
 DD_API int dd_batch_beam_config(const dd_batch *batch, int32_t beam, int32_t *config);
 
 /* Choose the persistent launch's tile configuration (0-6, dd_plan_set_tile's

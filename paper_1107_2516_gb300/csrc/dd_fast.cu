@@ -939,6 +939,7 @@ struct dd_batch {
     dd::LaneLaunch *d_lbeams = nullptr, *h_lbeams = nullptr; // the same for kernel 3 configurations
     dd::ShareLaunch *d_sbeams = nullptr, *h_sbeams = nullptr; // kernel 5 beams of the mixed configuration
     std::vector<int> kind;                 // mixed configuration: 1 = the beam runs kernel 5
+    std::vector<int> k5;                   // mixed configuration, own launches: the kernel 5 shape each beam runs
     bool per_beam = false;                 // launch mode: each beam's own kernel launch instead of one persistent grid
     unsigned int *d_counter = nullptr;
     int *d_err = nullptr;
@@ -1020,9 +1021,17 @@ static int batch_build(dd_batch *B, int k)
             bar_off = std::max(bar_off, fp(p)->sh[kMixedShare].bar_off);
         }
     }
+    B->k5.assign(B->plans.size(), -1);
     if (k == kMixedCfg && B->per_beam) {
-        // own launches: every beam with kernel 5 tables runs kernel 5
-        for (int i : order) B->kind[i] = fp(B->plans[i])->sh[kMixedShare].ok ? 1 : 0;
+        // own launches: every beam with kernel 5 tables runs its first
+        // available kernel 5 shape in the order of measured speed (the shape
+        // it would start on alone), the others kernel 3's mixed shape
+        static const int k5pref[] = {kShareBeg + 3, kShareBeg + 2, kShareBeg + 0, kShareBeg + 1};
+        for (int i : order) {
+            B->kind[i] = 0;
+            for (int c : k5pref)
+                if (cfg_ok(fp(B->plans[i]), c)) { B->kind[i] = 1; B->k5[i] = c; break; }
+        }
     } else if (k == kMixedCfg) {
         // keep the shape's resident blocks per SM: the kernel 5 beams with the
         // largest shared-memory layouts go back to kernel 3 until they fit
@@ -1068,6 +1077,13 @@ static int batch_prepare(dd_batch *B)
         const int64_t ntile = (p->nsamp_out + c.tile - 1) / c.tile;
         int rc = ensure_partials_public(p, ntile * c.nblk);
         if (rc) return rc;
+        if (B->k5.size() == B->plans.size() && B->k5[i] >= kShareBeg) {
+            // the beam's own kernel 5 launch (a capture must not allocate)
+            const int j = B->k5[i] - kShareBeg;
+            const int64_t t5 = (p->nsamp_out + 32 * kShareCfg[j].ti - 1) / (32 * kShareCfg[j].ti);
+            rc = ensure_partials_public(p, t5 * fp(p)->sh[j].nblk);
+            if (rc) return rc;
+        }
     }
     return DD_OK;
 }
@@ -1089,7 +1105,7 @@ static int batch_enqueue(dd_batch *B, const void *const *ins, const int64_t *pit
             FastPlan *f = fp(p);
             if (((uintptr_t)ins[i] & 15u) || (pitches[i] % f->al))
                 return set_error(DD_ERR_ARG, "beam %d: input rows must be 16-byte aligned in a batch", i);
-            const int k = B->cfg != kMixedCfg ? B->cfg : B->kind[i] ? kMixedCfg : kNumFastCfg + kMixedLane;
+            const int k = B->cfg != kMixedCfg ? B->cfg : B->kind[i] ? B->k5[i] : kNumFastCfg + kMixedLane;
             rc = fast_run(p, k, f->dgroup, ins[i], pitches[i], outs[i], s);
             if (rc) return rc;
         }
@@ -1432,7 +1448,8 @@ int dd_batch_beam_config(const dd_batch *B, int32_t beam, int32_t *config)
     if (beam < 0 || beam >= (int32_t)B->plans.size()) return set_error(DD_ERR_ARG, "beam %d out of range", beam);
     *config = -1;
     if (B->cfg < 0 || std::find(B->k2.begin(), B->k2.end(), beam) == B->k2.end()) return DD_OK;
-    if (B->cfg == kMixedCfg) *config = B->kind[beam] ? kMixedCfg : kNumFastCfg + kMixedLane;
+    if (B->cfg == kMixedCfg)
+        *config = !B->kind[beam] ? kNumFastCfg + kMixedLane : B->per_beam ? B->k5[beam] : kMixedCfg;
     else *config = B->cfg;
     return DD_OK;
 }

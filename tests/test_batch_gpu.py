@@ -75,7 +75,11 @@ def test_batch_matches_single_plans_and_graph(beams, config, per_beam):
     assert cfg == (9 if config is None else config) and nitems > 0 and nsep == 0
     for i, p in enumerate(plans):
         bc = batch.beam_config(i)
-        assert bc == cfg or (cfg == 9 and bc == 5)
+        if cfg == 9:
+            # mixed: kernel 3's shape 5, or kernel 5 (own launches: the beam's first available kernel 5 shape)
+            assert bc in ((5, 9, 10, 11, 12) if per_beam else (5, 9))
+        else:
+            assert bc == cfg
         p.set_tile(bc, 8)
     ins, pitches, outs = _bufs(beams, plans)
     # each plan alone
