@@ -44,7 +44,7 @@ WORKLOAD = "lofar_f32"
 # (9.2901x); profiles/dedisp_kernel5_lofar_f32.md has the capture.
 PROFILED_TRAFFIC = {
     (12, 64): (20532279447, "3a8780081765a9ad56e0b7179081134c1d3b7b9e0bfaa6462f77918567714f50"),
-    (11, 64): (19788754284, "47296186ee106f29fe8f004600f003dc3a0f9563e95c4d205700ffb49c1fc64d"),
+    (11, 64): (19788754284, "3a8780081765a9ad56e0b7179081134c1d3b7b9e0bfaa6462f77918567714f50"),
 }
 # the kernel's device sources (a change to the host tables that alters the
 # staged row lengths, i.e. the bytes each copy moves, needs a new capture too)
