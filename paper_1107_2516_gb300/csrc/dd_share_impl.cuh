@@ -85,8 +85,8 @@ struct ShareLaunch {
 // uniform in the warp and changes only at pattern ends, and lane l sums
 // element row_start + l of each of its rows: whole rows RPS at a time with
 // the pattern's offsets set up once (every load of a step issued before its
-// stores), the remaining rows one at a time.
-template <typename Tin, typename R, int CS, int NW, int RPS = 4>
+// stores), then the pattern's leftover rows in predicated steps of LRS rows.
+template <typename Tin, typename R, int CS, int NW, int RPS = 4, int LRS = RPS>
 __device__ __forceinline__ void share_stage1(const int32_t *rec, const Tin *srow, float *Pb, int warp, int lane)
 {
     static_assert(NW <= R::kMaxWarps, "stage-1 split recorded for at most kMaxWarps warps");
@@ -126,13 +126,25 @@ __device__ __forceinline__ void share_stage1(const int32_t *rec, const Tin *srow
                 Pb[e0 + ((r + u) << 5)] = v;
             }
         }
-        for (; r < rend; ++r) {
-            const int o = r << 5;
-            if (e0 + o < pend) {
-                float v = lane_ld<Tin>(srow + (src[0] + o));
+        for (; r < rend; r += LRS) {
+            // the pattern's leftover rows (fewer than RPS whole rows and the
+            // partial last one), LRS per step; only the rows and lanes inside
+            // the pattern load and store
+            float x[LRS][CS];
+            bool in[LRS];
 #pragma unroll
-                for (int c = 1; c < CS; ++c) v += lane_ld<Tin>(srow + (src[c] + o));
-                Pb[e0 + o] = v;
+            for (int u = 0; u < LRS; ++u) {
+                const int o = (r + u) << 5;
+                in[u] = r + u < rend && e0 + o < pend;
+#pragma unroll
+                for (int c = 0; c < CS; ++c) x[u][c] = in[u] ? lane_ld<Tin>(srow + (src[c] + o)) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < LRS; ++u) {
+                float v = x[u][0];
+#pragma unroll
+                for (int c = 1; c < CS; ++c) v += x[u][c];
+                if (in[u]) Pb[e0 + ((r + u) << 5)] = v;
             }
         }
         r = rend;
@@ -603,8 +615,9 @@ __global__ void __launch_bounds__((NW + PW) * 32, 1) share_ws_kernel(ShareLaunch
             if (!ok) break;
             const int32_t *rec = srec + (size_t)ib * R::kLen;
             int32_t *slot = slots + (size_t)pb * slot_len;
-            share_stage1<Tin, R, CS, PW, 8>(rec, rows + (size_t)ib * stage_elems,
-                                            reinterpret_cast<float *>(slot + kDmBlk), warp, lane);
+            // whole rows 8 per step (no accumulators here), leftovers 4 per step
+            share_stage1<Tin, R, CS, PW, 8, 4>(rec, rows + (size_t)ib * stage_elems,
+                                               reinterpret_cast<float *>(slot + kDmBlk), warp, lane);
             if (warp == PW - 1)
                 for (int j = lane; j < kDmBlk; j += 32) slot[j] = rec[R::kTrial + j];
             __syncwarp();
