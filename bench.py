@@ -43,8 +43,8 @@ WORKLOAD = "lofar_f32"
 # full launch: reads by the tile count (9.2581x), writes by the output count
 # (9.2901x); profiles/dedisp_kernel5_lofar_f32.md has the capture.
 PROFILED_TRAFFIC = {
-    (12, 64): (20545902320, "5a658a63c0dedb501efa8813742738fb34f454d160254218d18f90c987c3213b"),
-    (11, 64): (20128154371, "5a658a63c0dedb501efa8813742738fb34f454d160254218d18f90c987c3213b"),
+    (12, 64): (13982494111, "88eaa72c6d055f3e6e4d616657b71096ac879d87a0ffec8976a576ca6db5e24b"),
+    (11, 64): (14441256410, "88eaa72c6d055f3e6e4d616657b71096ac879d87a0ffec8976a576ca6db5e24b"),
 }
 # the kernel's device sources (a change to the host tables that alters the
 # staged row lengths, i.e. the bytes each copy moves, needs a new capture too)

@@ -686,6 +686,7 @@ static int share_run(dd_plan *p, int k, int dgroup, const void *in, int64_t pitc
     a.ntile = tile_hi - tile_lo; a.t_base = tile_lo * tile;
     a.dgroup = std::max(1, std::min(dgroup, c.nblk));
     a.out = out; a.err = f->d_err; a.smem = c.smem;
+    a.skew = tile_lo == 0 && tile_hi == ntile ? 1 : 0;   // whole-plan launches only (a tile range must stay in range)
     a.partials = static_cast<char *>(p->d_partials) + (size_t)(tile_lo * c.nblk) * stat_bytes(p);
     cudaError_t e = share_launch(k, p->dtype, a, s);
     if (e != cudaSuccess) return cuda_fail(e, "launch share_kernel");

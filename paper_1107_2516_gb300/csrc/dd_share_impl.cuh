@@ -76,7 +76,29 @@ struct ShareLaunch {
     void *out, *partials;
     int *err;
     size_t smem;
+    int skew;              // 1: DM block b takes the time tiles in a rotated order (share_raster)
 };
+
+// DM block / time tile of linear block index `lin`, as lane_raster, and with
+// a.skew set (a launch over every time tile of the plan) each DM block's
+// tiles rotated back by its own delay offset: block b takes tile (s - k_b)
+// mod ntile where lane_raster gives tile s, k_b = the block's row start in
+// the middle channel in whole tiles.  Blocks that run at the same time then
+// stage nearly the same input columns instead of windows up to the whole
+// delay span apart, so the staged input stays in L2 between them.  A
+// permutation of each block's tiles: every (block, tile) is still taken once.
+template <int TI>
+__device__ __forceinline__ void share_raster(const ShareLaunch &a, int64_t lin, int &blk, int64_t &t0)
+{
+    LaneLaunch r{};
+    r.dgroup = a.dgroup; r.ntile = a.ntile; r.nblk = a.nblk;
+    lane_raster<TI>(r, lin, blk, t0);
+    if (a.skew) {
+        constexpr int64_t kTile = 32 * TI;
+        const int64_t k = ((int64_t)a.base[(size_t)blk * a.nchans + a.nchans / 2] / kTile) % a.ntile;
+        t0 = ((t0 / kTile + a.ntile - k) % a.ntile) * kTile;
+    }
+}
 
 // Stage 1 of one subband: P[e] for e < E (the patterns' sums end to end).
 // Each pattern's sums form rows of 32 consecutive e (the last one partial);
@@ -339,12 +361,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) share_kernel(ShareLaunch a)
     __syncthreads();
     int blk;
     int64_t t0;
-    {
-        LaneLaunch r{};
-        r.dgroup = a.dgroup; r.ntile = a.ntile; r.nblk = a.nblk;
-        lane_raster<TI>(r, blockIdx.x, blk, t0);
-        t0 += a.t_base;
-    }
+    share_raster<TI>(a, blockIdx.x, blk, t0);
+    t0 += a.t_base;
     uint32_t gstage = 0;
     share_tile<Tin, kInt, TI, DR, NW, CS, NPMAX, NS>(a, blk, t0, blockIdx.x, bar, gstage);
 }
@@ -544,12 +562,8 @@ __global__ void __launch_bounds__((NW + PW) * 32, 1) share_ws_kernel(ShareLaunch
     __syncthreads();
     int blk;
     int64_t t0;
-    {
-        LaneLaunch r{};
-        r.dgroup = a.dgroup; r.ntile = a.ntile; r.nblk = a.nblk;
-        lane_raster<TI>(r, blockIdx.x, blk, t0);
-        t0 += a.t_base;
-    }
+    share_raster<TI>(a, blockIdx.x, blk, t0);
+    t0 += a.t_base;
 
     if (warp < PW) {
         // ---- stage 1 (and the input copies)
