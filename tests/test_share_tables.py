@@ -197,3 +197,27 @@ def test_stage1_rows_cover_every_sum_once_lofar():
             for s in range(0, rec.shape[1], 16):
                 assert np.all(_stage1_rows(rec[b, s], db, nw, W0[config]) == 1), (config, b, s)
 
+
+
+def test_tile_rotation_is_a_permutation():
+    # whole-plan kernel 5 launches rotate each DM block's time tiles back by
+    # its middle-channel row start in whole tiles (k_b); restated here on the
+    # benchmark plan's tables: every (block, tile) pair is taken exactly once,
+    # and the rotations spread the blocks over the delay span they stage
+    wl = synth.workload("lofar_f32")
+    d, m = oracle.delays(wl.nchans, wl.fch1, wl.foff, wl.tsamp, wl.dm_list)
+    nout = wl.nsamp - int(m)
+    for config in (11, 12):
+        t = ddc.dd_share_tables(np.asarray(d), wl.foff, dd.DD_F32, config)
+        tile, _ = SHAPES[config]
+        base = t["base"]
+        nblk, nch = base.shape
+        ntile = -(-nout // tile)
+        k = (base[:, nch // 2].astype(np.int64) // tile) % ntile
+        s = np.arange(ntile)
+        taken = (s[None, :] + ntile - k[:, None]) % ntile          # tile of slot s, per block
+        assert all(np.array_equal(np.sort(row), s) for row in taken)
+        # the rotations follow the middle channel's delay: monotone over the blocks,
+        # from 0 at DM 0 to about half the maxshift (in tiles) at the top
+        assert k[0] == 0 and np.all(np.diff(k) >= 0)
+        assert 0.3 * m / tile < k[-1] < 0.7 * m / tile
